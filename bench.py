@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: L.A.Cosmic Mpix/s at niter=4 on a 9576 x 6388 uint16 frame.
+
+Workload: the 61-Mpx uint16 large-format CMOS frame (seed 1; sky 300 ADU,
+gain 0.8, rn 1.2, ~4000 stars, 150000 cosmic-ray tracks, 0.5% salt-and-
+pepper), sigclip 4.5, sigfrac 0.3, objlim 5, niter 4, one frame per call.
+A step is one full detect-and-clean of the frame (all iterations plus the
+final mask/cleaned write).  Inputs are resident in HBM when timing starts;
+L2 is flushed (a 256 MiB write) between timed steps.  With --gpus N (under
+torchrun) every rank cleans its own frame: weak scaling, no collective.
+
+--impl reference times the float32 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "lacosmic_9576x6388_u16_niter4"
+METRIC = "L.A.Cosmic Mpix/s at niter=4 on 61-Mpx frames"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(self.out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- CPU oracle ----
+def oracle_sample(frame, spec, seconds_target=12.0, crop=256):
+    """Time the float32 CPU oracle on crops of the frame (one core)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    ny, nx = frame.shape
+    rng = np.random.default_rng(123)
+    done_px, t_total, n = 0, 0.0, 0
+    while t_total < seconds_target and n < 64:
+        y0 = int(rng.integers(0, ny - crop))
+        x0 = int(rng.integers(0, nx - crop))
+        c = np.ascontiguousarray(frame[y0:y0 + crop, x0:x0 + crop])
+        t0 = time.perf_counter()
+        oracle.run(c, spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac,
+                   spec.objlim, spec.niter)
+        t_total += time.perf_counter() - t0
+        done_px += crop * crop
+        n += 1
+    return {"value": done_px / 1e6 / t_total, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} crops of {crop}x{crop} px from the workload frame, niter=4, "
+                      f"single-threaded float32 C++ oracle, {t_total:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2602_17938_gb300 import synth
+    spec = synth.config_specs(1)[0]
+    frame = synth.make_frame(spec)
+    import numpy as np
+    import oracle
+    oracle.build()
+    crop = 192
+    rng = np.random.default_rng(7)
+    ny, nx = frame.shape
+
+    def step():
+        y0, x0 = int(rng.integers(0, ny - crop)), int(rng.integers(0, nx - crop))
+        c = np.ascontiguousarray(frame[y0:y0 + crop, x0:x0 + crop])
+        oracle.run(c, spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac,
+                   spec.objlim, spec.niter)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = args.steps * crop * crop / 1e6 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{crop}x{crop} crop per step",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one {crop}x{crop} crop of the workload frame per step, "
+                                       "niter=4, single-threaded float32 C++ oracle"},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm -----
+def alu_peak():
+    import ctypes
+    from paper_2602_17938_gb300 import build
+    lib = ctypes.CDLL(build.PEAK_LIB)
+    lib.alu_minmax_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+    f32, u16 = ctypes.c_double(), ctypes.c_double()
+    if lib.alu_minmax_peak(0, ctypes.byref(f32), ctypes.byref(u16)) != 0:
+        return None, None
+    return f32.value, u16.value
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_17938_gb300 import lacos, synth, netcost
+
+    spec = synth.config_specs(1)[0]
+    if rank:
+        spec.seed = (1, rank)
+    frame = synth.make_frame(spec)
+    ny, nx = frame.shape
+    npix = ny * nx
+    d_frame = lacos.to_device(frame, dev)
+    d_mask = torch.empty((ny, nx), dtype=torch.uint8, device=dev)
+    d_clean = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    params = lacos.make_params(spec.gain, spec.readnoise, spec.satlevel, spec.sigclip,
+                               spec.sigfrac, spec.objlim, spec.niter)
+    ctx = lacos.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.wait(ctx.submit(d_frame, params, d_mask, d_clean))
+    torch.cuda.synchronize()
+
+    ctx.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    tickets = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            tickets.append(ctx.submit(d_frame, params, d_mask, d_clean))
+            ev[i][1].record(stream)
+        profs = []
+        for t in tickets:
+            r = ctx.wait(t)
+            profs.append(ctx.last_profile())
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier()
+    ctx.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * npix * args.steps / 1e6 / total_s
+
+    # Roofline of the dominant kernel (detect), from the live per-launch profile.
+    det_ms = [ms for p in profs for ms in p["detect_ms"]]
+    fin_ms = [p["finalize_ms"] for p in profs]
+    n_launch = len(det_ms)
+    ops = sum(netcost.detect_minmax_ops(p) for p in profs)
+    det_avg_ms = sum(det_ms) / max(1, n_launch)
+    achieved = ops / n_launch / (det_avg_ms * 1e-3) / 1e12 if n_launch else None
+    peak_f32, peak_u16 = alu_peak()
+    peak = peak_f32 / 1e3 if peak_f32 else None
+    share = sum(det_ms) / (sum(det_ms) + sum(fin_ms))
+
+    # End to end through the public API: pinned host frame in, mask+cleaned out.
+    h_frame = torch.from_numpy(frame.view(np.int16)).pin_memory().view(torch.uint16)
+    h_mask = torch.empty((ny, nx), dtype=torch.uint8).pin_memory()
+    h_clean = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        lacos.clean_host(h_frame, params, h_mask, h_clean, ctx=ctx, work=(d_frame, d_mask, d_clean))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        lacos.clean_host(h_frame, params, h_mask, h_clean, ctx=ctx, work=(d_frame, d_mask, d_clean))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * npix * args.e2e_steps / 1e6 / e2e_s
+
+    ok_check = bool(np.array_equal(h_clean.numpy()[h_mask.numpy() == 0],
+                                   frame[h_mask.numpy() == 0].astype(np.float32)))
+    ctx.close()
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else oracle_sample(frame, spec)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ny": ny, "nx": nx, "frame_dtype": "u16", "niter": spec.niter,
+                   "frames_per_call": 1, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tminmax/s",
+                     "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                     "kernel": "detect_kernel", "peak_source": "measured min.f32/max.f32 issue rate",
+                     "avg_launch_ms": det_avg_ms, "launch_share": share},
+        "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": 2 * npix,
+                "d2h_bytes_per_step": 5 * npix},
+        "gpu_launches": args.steps * (spec.niter + 1),
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+        "check_clean_equals_input_outside_mask": ok_check,
+        "alu_peak_gops": {"f32": peak_f32, "u16x2": peak_u16},
+        "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_fine", "n_replace")},
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * lacos.h -- C ABI of the GB300 L.A.Cosmic detect-and-clean library.
+ *
+ * The operation is the cosmic-ray detection and cleaning iteration of
+ * L.A.Cosmic (van Dokkum 2001) as ported by dfcosmic (arXiv 2602.17938,
+ * Methods / "Algorithm", steps 1-7, and "Main parameters"):
+ *   1. Laplacian detection: the image is block-replicated 2x, convolved with
+ *      the 3x3 Laplacian, clipped at zero and block-averaged back (L+);
+ *   2. noise model N = sqrt(max(gain*med5(I), 1e-4) + readnoise^2) / gain;
+ *   3. significance S = L+ / (2N), and S' = S - med5(S);
+ *   4. candidates: S' > sigclip;
+ *   5. compact objects rejected: S'/F > objlim with the fine-structure image
+ *      F = max((med3(I) - med7(med3(I))) / N, 0.01);
+ *   6. neighbours included by two 3x3 growth steps re-tested against sigclip
+ *      and sigfrac*sigclip; saturated pixels (input >= satlevel) never flag;
+ *   7. flagged pixels replaced by the median of the unflagged input pixels
+ *      of their 5x5 window (lower median for even counts; widened to 7x7,
+ *      9x9, ... when none is unflagged);
+ * repeated up to niter times, stopping early once an iteration flags no new
+ * pixel.  Medians are true (non-separable) K x K medians with clamp-to-edge
+ * borders.  Arithmetic is IEEE float32 (no FMA contraction), and results are
+ * bit-identical to a plain float32 CPU implementation of the same steps.
+ *
+ * Layout: every image is row-major, ny rows of nx pixels, row stride nx,
+ * contiguous, in device memory (except where a call says "host").
+ *
+ * Ownership: the caller owns frames and outputs and keeps them alive and
+ * untouched from submit until poll reports completion.  The library owns
+ * its scratch (2 bits per pixel plus a few hundred bytes per request),
+ * charged against the context's HBM budget.
+ *
+ * Errors: every call returns an int status; 0 is success.  Negative values
+ * are the LACOS_E* codes below; lacos_poll also returns LACOS_PENDING (1).
+ * Calls are thread-safe on one context.
+ */
+#ifndef LACOS_H
+#define LACOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lacos_ctx lacos_ctx; /* opaque, library-owned */
+typedef struct CUstream_st *lacos_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum { LACOS_F32 = 0, LACOS_U16 = 1 } lacos_dtype;
+
+enum {
+  LACOS_OK = 0,
+  LACOS_PENDING = 1,
+  LACOS_EINVAL = -1,          /* bad pointer, size or parameter */
+  LACOS_EAGAIN = -2,          /* no free slot or budget right now: retry later */
+  LACOS_ENOMEM = -3,          /* the request can never fit the context's budget */
+  LACOS_ECUDA = -4,           /* a CUDA call failed; see lacos_last_cuda_error */
+  LACOS_ENONFINITE = -5,      /* the input held NaN or Inf: outputs undefined */
+  LACOS_ETIMEOUT = -6,        /* a bounded device wait gave up */
+  LACOS_EUNKNOWN_TICKET = -7  /* poll on a ticket that is not in flight */
+};
+
+#define LACOS_MAX_NITER 256
+
+/* Parameters of one frame (dfcosmic "Main parameters" plus gain, readnoise).
+ * gain > 0 [e-/ADU]; readnoise >= 0 [e-]; satlevel [ADU], <= 0 disables the
+ * saturation guard; sigclip, sigfrac, objlim > 0; 0 <= niter <= 256.
+ * fine_norm: 1 divides the fine-structure image by N (default reading),
+ * 0 uses max(med3 - med7, 0.01) unnormalised. */
+typedef struct {
+  float gain, readnoise, satlevel, sigclip, sigfrac, objlim;
+  int niter;
+  int fine_norm;
+} lacos_params;
+
+typedef struct {
+  int status;            /* LACOS_OK or LACOS_ENONFINITE / LACOS_ETIMEOUT */
+  int iters_run;         /* iterations executed (early stop included) */
+  long long n_flagged;   /* pixels in the final cosmic-ray mask */
+  double latency_ms;     /* submit-to-completion on the device (event time) */
+} lacos_result;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * library-owned scratch (0 = 8 GiB); max_slots caps requests in flight
+ * (0 = 64).  *out receives the context. */
+int lacos_create(lacos_ctx **out, int device, size_t hbm_budget_bytes, int max_slots);
+
+/* Queue the detect-and-clean of one frame on `stream` (work is ordered
+ * after everything already queued on it; the outputs are complete when the
+ * completion event recorded on `stream` fires).
+ *   d_frame : ny*nx float32 (LACOS_F32) or uint16 (LACOS_U16) pixels [ADU]
+ *   d_mask  : out, ny*nx uint8, 1 = cosmic ray (cumulative over iterations)
+ *   d_clean : out, ny*nx float32 cleaned frame
+ *   ticket  : out, identifies the request for lacos_poll
+ * Requires 1 <= ny, nx and ny*nx < 2^31.  Returns LACOS_EAGAIN when no slot
+ * or budget is free (nothing was queued). */
+int lacos_submit(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int nx,
+                 const lacos_params *p, uint8_t *d_mask, float *d_clean,
+                 lacos_stream stream, unsigned long long *ticket);
+
+/* Non-blocking completion check.  Returns LACOS_PENDING while the request
+ * runs; otherwise fills *res, releases the request's slot and returns
+ * LACOS_OK (res->status carries LACOS_ENONFINITE/LACOS_ETIMEOUT if the device
+ * reported one).  A ticket can be polled to completion once. */
+int lacos_poll(lacos_ctx *c, unsigned long long ticket, lacos_result *res);
+
+/* Block until the request completes, then behave as lacos_poll. */
+int lacos_wait(lacos_ctx *c, unsigned long long ticket, lacos_result *res);
+
+/* Batched form: n frames of any sizes and dtypes processed together, one
+ * launch per iteration level over a shared tile work queue (and a CUDA
+ * graph replayed when the same batch is submitted again with
+ * reuse_graph != 0).  Arrays have n entries; params may differ per frame
+ * (niter included).  One ticket covers the whole batch; its lacos_result
+ * sums n_flagged and reports the largest iters_run; per-frame results go
+ * to per_frame (host array of n, may be NULL) when the batch is polled. */
+int lacos_submit_batch(lacos_ctx *c, int n, const void *const *d_frames, const int *dtypes,
+                       const int *ny, const int *nx, const lacos_params *params,
+                       uint8_t *const *d_masks, float *const *d_cleans, lacos_stream stream,
+                       int reuse_graph, lacos_result *per_frame, unsigned long long *ticket);
+
+/* Kernel-level profile of the most recent request completed on the context
+ * (filled only while profiling is switched on with lacos_set_profiling; the
+ * times come from CUDA events recorded between the request's launches on
+ * its stream, so requests replayed from a CUDA graph are not profiled). */
+typedef struct {
+  int n_detect;                        /* detect launches (one per iteration level) */
+  float detect_ms[LACOS_MAX_NITER];    /* device time of each detect launch */
+  float finalize_ms;                   /* device time of the finalize launch */
+  long long px_iterations;             /* sum over frames of ny*nx*iters_run */
+  long long n_sprime;                  /* pixels where S' = S - med5(S) was evaluated */
+  long long n_fine;                    /* pixels where the fine-structure F was evaluated */
+  long long n_replace;                 /* masked-median replacements inside detect launches */
+} lacos_profile;
+
+int lacos_set_profiling(lacos_ctx *c, int on);
+int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
+
+/* Drain in-flight work, free all library memory and the context. */
+int lacos_destroy(lacos_ctx *c);
+
+/* Scratch bytes a frame of ny x nx needs (what the budget is charged). */
+size_t lacos_scratch_bytes(int ny, int nx);
+
+/* Last CUDA error code seen by the context (0 if none). */
+int lacos_last_cuda_error(lacos_ctx *c);
+
+/* Library version string. */
+const char *lacos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LACOS_H */

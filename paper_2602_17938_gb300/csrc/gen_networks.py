@@ -1,0 +1,326 @@
+"""Generator for the branch-free min/max selection networks used by the kernels.
+
+Writes ``networks.cuh``.  Every network is straight-line code of two-input
+``MN``/``MX`` (min/max) operations in SSA form, so the same text serves any
+key type that defines them (float, 32-bit integers, packed u16x2).
+
+Construction (standard results, written from their definitions):
+  * K. E. Batcher's odd-even merge (1968) for merging sorted lists of any
+    length, applied recursively to sort;
+  * the separable "sort columns, then merge" median of Adams (2021, ACM TOG
+    40(4), "Fast median filters using separable sorting networks"): a K x K
+    median is the rank-(K*K-1)/2 element of the union of K sorted columns,
+    and neighbouring outputs share column sorts and partial merges;
+  * dead-code pruning: only operations that feed a requested output are
+    emitted, a comparator whose max (or min) is unused costs one operation,
+    and operations on +/-infinity sentinels are folded away.
+
+Run as a script to regenerate the header; the tests re-run ``verify()``.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+import random
+import sys
+
+NEG, POS = "-inf", "+inf"
+
+
+class Dag:
+    """SSA min/max DAG with constant folding and common-subexpression reuse."""
+
+    def __init__(self):
+        self.ops = []  # (kind, a, b) ; node id = index + n_inputs offset via names
+        self.memo = {}
+        self.names = []  # node names: inputs are ("in", k)
+
+    def inp(self, label):
+        self.names.append(("in", label))
+        return len(self.names) - 1
+
+    def _op(self, kind, a, b):
+        if a == b:
+            return a
+        if kind == "min":
+            if a == NEG or b == NEG:
+                return NEG
+            if a == POS:
+                return b
+            if b == POS:
+                return a
+        else:
+            if a == POS or b == POS:
+                return POS
+            if a == NEG:
+                return b
+            if b == NEG:
+                return a
+        key = (kind, min(a, b, key=str), max(a, b, key=str))
+        if key in self.memo:
+            return self.memo[key]
+        self.names.append((kind, a, b))
+        nid = len(self.names) - 1
+        self.memo[key] = nid
+        return nid
+
+    def mn(self, a, b):
+        return self._op("min", a, b)
+
+    def mx(self, a, b):
+        return self._op("max", a, b)
+
+    def cmpx(self, lst, i, j):
+        a, b = lst[i], lst[j]
+        lst[i], lst[j] = self.mn(a, b), self.mx(a, b)
+
+    # -- Batcher odd-even merge of two sorted lists (any lengths) ------------
+    def merge(self, a, b):
+        """Merge sorted lists a and b into one sorted list (Batcher)."""
+        if not a:
+            return list(b)
+        if not b:
+            return list(a)
+        if len(a) == 1 and len(b) == 1:
+            return [self.mn(a[0], b[0]), self.mx(a[0], b[0])]
+        # pad both to a common power of two with +inf so the classic
+        # recursion applies; the sentinels fold away.
+        n = 1
+        while n < max(len(a), len(b)):
+            n *= 2
+        A = list(a) + [POS] * (n - len(a))
+        B = list(b) + [POS] * (n - len(b))
+        out = self._merge_pow2(A, B)
+        return out[:len(a) + len(b)]
+
+    def _merge_pow2(self, A, B):
+        n = len(A)
+        if n == 1:
+            return [self.mn(A[0], B[0]), self.mx(A[0], B[0])]
+        ev = self._merge_pow2(A[0::2], B[0::2])
+        od = self._merge_pow2(A[1::2], B[1::2])
+        out = [ev[0]]
+        for i in range(1, n):
+            x, y = od[i - 1], ev[i]
+            out += [self.mn(x, y), self.mx(x, y)]
+        out.append(od[n - 1])
+        return out
+
+    def sort(self, lst):
+        lst = list(lst)
+        if len(lst) <= 1:
+            return lst
+        h = len(lst) // 2
+        return self.merge(self.sort(lst[:h]), self.sort(lst[h:]))
+
+    def sort5(self, v):
+        """Optimal 9-comparator network for 5 keys (verified by the 0-1 principle)."""
+        v = list(v)
+        for i, j in ((0, 1), (3, 4), (2, 4), (2, 3), (1, 4), (0, 3), (0, 2), (1, 3), (1, 2)):
+            self.cmpx(v, i, j)
+        return v
+
+    def sort3(self, v):
+        v = list(v)
+        for i, j in ((0, 1), (1, 2), (0, 1)):
+            self.cmpx(v, i, j)
+        return v
+
+    def sortk(self, v):
+        if len(v) == 3:
+            return self.sort3(v)
+        if len(v) == 5:
+            return self.sort5(v)
+        return self.sort(v)
+
+    def select2(self, A, B, k):
+        """Rank-k element of the union of sorted A and B, as the minimum over
+        the k+1-element prefixes (i from A, k+1-i from B) of their largest
+        member: min_i max(A[i-1], B[k-i])."""
+        terms = []
+        for i in range(0, len(A) + 1):
+            j = k + 1 - i
+            if j < 0 or j > len(B):
+                continue
+            a = A[i - 1] if i >= 1 else NEG
+            b = B[j - 1] if j >= 1 else NEG
+            terms.append(self.mx(a, b))
+        out = terms[0]
+        for t in terms[1:]:
+            out = self.mn(out, t)
+        return out
+
+    def select_rank(self, lists, rank):
+        """Element of rank ``rank`` (0-based) in the union of sorted lists."""
+        lists = [l for l in lists if l]
+        while len(lists) > 1:
+            lists.sort(key=len)
+            a, b = lists[0], lists[1]
+            lists = lists[2:] + [self.merge(a, b)]
+        return lists[0][rank]
+
+
+def live_ops(dag: Dag, outputs):
+    """Ids of operation nodes that feed ``outputs`` (after pruning)."""
+    live = set()
+    stack = [o for o in outputs if isinstance(o, int)]
+    while stack:
+        n = stack.pop()
+        if n in live:
+            continue
+        live.add(n)
+        nm = dag.names[n]
+        if nm[0] != "in":
+            for c in nm[1:]:
+                if isinstance(c, int):
+                    stack.append(c)
+    return sorted(x for x in live if dag.names[x][0] != "in")
+
+
+def count_ops(dag, outputs):
+    return len(live_ops(dag, outputs))
+
+
+def evaluate(dag: Dag, outputs, env):
+    """Evaluate outputs with Python values; env maps input label -> value."""
+    val = {}
+    big = float("inf")
+
+    def get(x):
+        if x == NEG:
+            return -big
+        if x == POS:
+            return big
+        return val[x]
+
+    for i, nm in enumerate(dag.names):
+        if nm[0] == "in":
+            val[i] = env[nm[1]]
+    for i in live_ops(dag, outputs):
+        k, a, b = dag.names[i]
+        val[i] = min(get(a), get(b)) if k == "min" else max(get(a), get(b))
+    return [get(o) for o in outputs]
+
+
+# ---------------------------------------------------------------------------
+# Networks
+# ---------------------------------------------------------------------------
+
+def window_median(K):
+    """Standalone K x K median: sort columns, then select the middle rank.
+
+    For K = 5 the four right-hand columns are merged pairwise, the two pairs
+    merged, and the rank-12 element of that list and the first column is
+    taken with ``select2``; other K use merges throughout."""
+    d = Dag()
+    cols = []
+    for c in range(K):
+        col = [d.inp((r, c)) for r in range(K)]
+        cols.append(d.sortk(col))
+    M = (K * K - 1) // 2
+    if K == 5:
+        q = d.merge(d.merge(cols[1], cols[2]), d.merge(cols[3], cols[4]))
+        out = d.select2(q, cols[0], M)
+    else:
+        out = d.select_rank(cols, M)
+    return d, [out]
+
+
+def flat_median(n):
+    """Median (rank (n-1)//2) of n loose keys: pruned Batcher sort."""
+    d = Dag()
+    v = [d.inp(i) for i in range(n)]
+    s = d.sort(v)
+    return d, [s[(n - 1) // 2]]
+
+
+def emit_function(name, dag, outputs, in_shape, doc):
+    """Emit a __device__ template taking inputs v[...] and writing o[...]."""
+    lines = [f"// {doc}", f"// {count_ops(dag, outputs)} min/max operations.",
+             "template <class K>",
+             f"__device__ __forceinline__ void {name}(const K* __restrict__ v, K* __restrict__ o) {{"]
+    ids = live_ops(dag, outputs)
+    names = {}
+    for i, nm in enumerate(dag.names):
+        if nm[0] == "in":
+            lab = nm[1]
+            if isinstance(lab, tuple):
+                idx = 0
+                for k, dim in zip(lab, in_shape):
+                    idx = idx * dim + k
+            else:
+                idx = lab
+            names[i] = f"v[{idx}]"
+
+    def ref(x):
+        if x == NEG:
+            return "lacos_net::neg_inf<K>()"
+        if x == POS:
+            return "lacos_net::pos_inf<K>()"
+        return names[x]
+
+    for i in ids:
+        k, a, b = dag.names[i]
+        names[i] = f"t{i}"
+        fn = "MN" if k == "min" else "MX"
+        lines.append(f"  const K t{i} = {fn}({ref(a)}, {ref(b)});")
+    for j, o in enumerate(outputs):
+        lines.append(f"  o[{j}] = {ref(o)};")
+    lines.append("}")
+    return "\n".join(lines)
+
+
+def build_all():
+    nets = {}
+    nets["med3x3"] = window_median(3) + ((3, 3), "Median of a 3x3 window, v row-major.")
+    nets["med5x5"] = window_median(5) + ((5, 5), "Median of a 5x5 window, v row-major.")
+    nets["med7x7"] = window_median(7) + ((7, 7), "Median of a 7x7 window, v row-major.")
+    return nets
+
+
+def verify(nets=None, trials=2000, seed=1):
+    """Check every network against a full sort (random keys with ties, 0-1 keys)."""
+    nets = nets or build_all()
+    rng = random.Random(seed)
+    for name, (dag, outs, shape, _) in nets.items():
+        labels = [nm[1] for nm in dag.names if nm[0] == "in"]
+        n = len(labels)
+        for t in range(trials):
+            hi = [1, 3, 1000][t % 3]
+            vals = [rng.randint(0, hi) for _ in labels]
+            env = dict(zip(labels, vals))
+            got = evaluate(dag, outs, env)[0]
+            exp = sorted(vals)[(n - 1) // 2]
+            if got != exp:
+                raise AssertionError(f"{name}: got {got}, expected {exp} for {vals}")
+        if n <= 20:
+            for bits in itertools.product((0, 1), repeat=n):
+                env = dict(zip(labels, bits))
+                if evaluate(dag, outs, env)[0] != sorted(bits)[(n - 1) // 2]:
+                    raise AssertionError(f"{name}: 0-1 failure")
+    return True
+
+
+HEADER = """// Generated by gen_networks.py -- do not edit.
+// Branch-free min/max selection networks (see the generator for the
+// construction and its sources).  MN/MX must be defined for the key type.
+#pragma once
+"""
+
+
+def main(out_path):
+    nets = build_all()
+    verify(nets, trials=500)
+    parts = [HEADER]
+    for name, (dag, outs, shape, doc) in nets.items():
+        parts.append(emit_function(name, dag, outs, shape, doc))
+    text = "\n\n".join(parts) + "\n"
+    with open(out_path, "w") as f:
+        f.write(text)
+    for name, (dag, outs, shape, doc) in nets.items():
+        print(f"{name}: {count_ops(dag, outs)} ops")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else
+         os.path.join(os.path.dirname(os.path.abspath(__file__)), "networks.cuh"))

@@ -1,0 +1,462 @@
+// Runtime and C ABI of the L.A.Cosmic library (declared in include/lacos.h).
+//
+// A context owns a fixed set of slots.  A submitted request (one frame or a
+// batch) takes a free slot, whose device scratch -- per-frame descriptors,
+// per-frame state, two bit-packed mask buffers per frame and the tile-queue
+// heads -- is allocated stream-ordered and charged against the context's
+// HBM budget.  The request's work is queued on the caller's stream:
+//   memcpy(descriptors) ; memset(state, heads, M_0) ;
+//   detect_kernel(k) for k = 1..max niter ; finalize_kernel ;
+//   memcpy(state -> pinned host) ; event.
+// Polling queries the event, reads the pinned state and frees the slot.
+// Iteration control is on the device: an iteration whose predecessor
+// flagged nothing returns at once, so the host never waits mid-request.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "lacos_kernels.cuh"
+
+using namespace lacos;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+struct FrameReq {
+  const void* frame;
+  int dtype, ny, nx;
+  lacos_params p;
+  uint8_t* mask;
+  float* clean;
+};
+
+struct Slot {
+  bool busy = false;
+  unsigned long long ticket = 0;
+  void* dscratch = nullptr;  // device scratch
+  size_t dcap = 0;
+  void* hpinned = nullptr;   // pinned host staging (descriptors in, states out)
+  size_t hcap = 0;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  int nframes = 0;
+  lacos_result* per_frame = nullptr;  // caller's array for batch results
+  // CUDA graph of the last batch (replayed when the same batch comes back).
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<FrameReq> graph_key;
+  cudaStream_t graph_stream = nullptr;
+  // Profiling events: [0] before the first detect, [k] after detect k, [n+1] after finalize.
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_n = -1;  // detect launches recorded for the request in flight (-1: none)
+  std::vector<long long> npix;
+};
+
+bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i) {
+    if (a[i].frame != b[i].frame || a[i].dtype != b[i].dtype || a[i].ny != b[i].ny ||
+        a[i].nx != b[i].nx || a[i].mask != b[i].mask || a[i].clean != b[i].clean ||
+        std::memcmp(&a[i].p, &b[i].p, sizeof(lacos_params)) != 0)
+      return false;
+  }
+  return true;
+}
+
+int wpr_of(int nx) { return (nx + 31) / 32; }
+size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
+
+struct Layout {
+  size_t heads, descs, states, masks, total;
+  std::vector<size_t> mask_off;
+};
+
+Layout layout_for(const std::vector<FrameReq>& fr) {
+  Layout L;
+  const size_t n = fr.size();
+  L.heads = 0;
+  L.descs = align_up(sizeof(unsigned) * (LACOS_MAX_NITER + 2));
+  L.states = L.descs + align_up(sizeof(FrameDesc) * n);
+  L.masks = L.states + align_up(sizeof(FrameState) * n);
+  size_t off = L.masks;
+  for (const auto& f : fr) {
+    L.mask_off.push_back(off);
+    off += 2 * maskbuf_bytes(f.ny, f.nx);
+  }
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct lacos_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t charged = 0;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  unsigned long long next_ticket = 1;
+  std::atomic<int> last_cuda{0};
+  int num_sms = 0;
+  int blocks_per_sm_detect = 1;
+  int blocks_per_sm_final = 1;
+  bool profiling = false;
+  lacos_profile last_prof{};
+};
+
+static int cuda_fail(lacos_ctx* c, cudaError_t e) {
+  if (c) c->last_cuda = (int)e;
+  return LACOS_ECUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_); \
+  } while (0)
+
+static bool params_valid(const lacos_params* p) {
+  if (!p) return false;
+  const float v[6] = {p->gain, p->readnoise, p->satlevel, p->sigclip, p->sigfrac, p->objlim};
+  for (float x : v)
+    if (!std::isfinite(x)) return false;
+  if (!(p->gain > 0.0f) || !(p->readnoise >= 0.0f) || !(p->sigclip > 0.0f) ||
+      !(p->sigfrac > 0.0f) || !(p->objlim > 0.0f))
+    return false;
+  if (p->niter < 0 || p->niter > LACOS_MAX_NITER) return false;
+  if (p->fine_norm != 0 && p->fine_norm != 1) return false;
+  return true;
+}
+
+static bool frame_valid(const FrameReq& f) {
+  if (!f.frame || !f.mask || !f.clean) return false;
+  if (f.dtype != LACOS_F32 && f.dtype != LACOS_U16) return false;
+  if (f.ny < 1 || f.nx < 1) return false;
+  if ((long long)f.ny * (long long)f.nx >= (1LL << 31)) return false;
+  return params_valid(&f.p);
+}
+
+// Frees idle slots' scratch until `need` more bytes fit the budget.
+static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
+  for (auto& sl : c->slots) {
+    if (c->charged + need <= c->budget) return;
+    if (!sl.busy && sl.dscratch) {
+      cudaFreeAsync(sl.dscratch, s);
+      c->charged -= sl.dcap;
+      sl.dscratch = nullptr;
+      sl.dcap = 0;
+      if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; sl.graph_key.clear(); }
+    }
+  }
+}
+
+static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, const Layout& L,
+                   cudaStream_t s, bool prof) {
+  char* d = (char*)sl.dscratch;
+  unsigned* heads = (unsigned*)(d + L.heads);
+  FrameDesc* ddesc = (FrameDesc*)(d + L.descs);
+  FrameState* dstate = (FrameState*)(d + L.states);
+  // Host descriptors in the pinned buffer (states come back after them).
+  FrameDesc* hdesc = (FrameDesc*)sl.hpinned;
+  unsigned total = 0;
+  int max_niter = 0;
+  for (size_t i = 0; i < fr.size(); ++i) {
+    const FrameReq& f = fr[i];
+    FrameDesc& h = hdesc[i];
+    std::memset(&h, 0, sizeof(h));
+    h.x0 = f.frame;
+    h.dtype = f.dtype;
+    h.ny = f.ny;
+    h.nx = f.nx;
+    h.wpr = wpr_of(f.nx);
+    h.mbuf0 = (uint32_t*)(d + L.mask_off[i]);
+    h.mbuf1 = (uint32_t*)(d + L.mask_off[i] + maskbuf_bytes(f.ny, f.nx));
+    h.mask_out = f.mask;
+    h.clean_out = f.clean;
+    h.st = dstate + i;
+    h.gain = f.p.gain;
+    volatile float rn = f.p.readnoise;
+    volatile float rn2 = rn * rn;  // float product, as the float32 definition
+    h.rn2 = rn2;
+    h.satlevel = f.p.satlevel;
+    h.sigclip = f.p.sigclip;
+    volatile float lo = f.p.sigfrac * f.p.sigclip;
+    h.lo = lo;
+    h.thr_min = std::min(h.lo, h.sigclip);
+    h.objlim = f.p.objlim;
+    h.niter = f.p.niter;
+    h.fnorm = f.p.fine_norm;
+    h.tiles_x = (f.nx + TW - 1) / TW;
+    const unsigned tiles = (unsigned)h.tiles_x * (unsigned)((f.ny + TH - 1) / TH);
+    h.tile_begin = total;
+    total += tiles;
+    h.tile_end = total;
+    max_niter = std::max(max_niter, f.p.niter);
+  }
+  CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(heads, 0, sizeof(unsigned) * (LACOS_MAX_NITER + 2), s));
+  CK(cudaMemsetAsync(dstate, 0, sizeof(FrameState) * fr.size(), s));
+  for (size_t i = 0; i < fr.size(); ++i)
+    CK(cudaMemsetAsync(d + L.mask_off[i], 0, maskbuf_bytes(fr[i].ny, fr[i].nx), s));
+  const int nf = (int)fr.size();
+  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_detect));
+  if (prof) {
+    while ((int)sl.prof_ev.size() < max_niter + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      sl.prof_ev.push_back(e);
+    }
+    CK(cudaEventRecord(sl.prof_ev[0], s));
+  }
+  for (int k = 1; k <= max_niter; ++k) {
+    detect_kernel<<<gd, NT, 0, s>>>(ddesc, nf, total, k, heads + k);
+    CK(cudaGetLastError());
+    if (prof) CK(cudaEventRecord(sl.prof_ev[k], s));
+  }
+  const unsigned gf = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
+  finalize_kernel<<<gf, NT, 0, s>>>(ddesc, nf, total, heads + LACOS_MAX_NITER + 1);
+  CK(cudaGetLastError());
+  if (prof) CK(cudaEventRecord(sl.prof_ev[max_niter + 1], s));
+  sl.prof_n = prof ? max_niter : -1;
+  FrameState* hstate = (FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * fr.size()));
+  CK(cudaMemcpyAsync(hstate, dstate, sizeof(FrameState) * fr.size(), cudaMemcpyDeviceToHost, s));
+  return LACOS_OK;
+}
+
+static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream_t s,
+                       int reuse_graph, lacos_result* per_frame, unsigned long long* ticket) {
+  if (!c || !ticket || fr.empty()) return LACOS_EINVAL;
+  for (const auto& f : fr)
+    if (!frame_valid(f)) return LACOS_EINVAL;
+  const Layout L = layout_for(fr);
+  const size_t hneed = align_up(sizeof(FrameDesc) * fr.size()) + sizeof(FrameState) * fr.size();
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (L.total > c->budget) return LACOS_ENOMEM;
+  CK(cudaSetDevice(c->device));
+  // Pick a free slot, preferring one whose scratch is already large enough.
+  Slot* sl = nullptr;
+  for (auto& x : c->slots)
+    if (!x.busy && x.dcap >= L.total) { sl = &x; break; }
+  if (!sl)
+    for (auto& x : c->slots)
+      if (!x.busy) { sl = &x; break; }
+  if (!sl) return LACOS_EAGAIN;
+  if (sl->dcap < L.total) {
+    if (sl->dscratch) {
+      CK(cudaFreeAsync(sl->dscratch, s));
+      c->charged -= sl->dcap;
+      sl->dscratch = nullptr;
+      sl->dcap = 0;
+      if (sl->gexec) { cudaGraphExecDestroy(sl->gexec); sl->gexec = nullptr; sl->graph_key.clear(); }
+    }
+    evict_idle(c, L.total, s);
+    if (c->charged + L.total > c->budget) return LACOS_EAGAIN;
+    CK(cudaMallocAsync(&sl->dscratch, L.total, s));
+    sl->dcap = L.total;
+    c->charged += L.total;
+  }
+  if (sl->hcap < hneed) {
+    if (sl->hpinned) { CK(cudaStreamSynchronize(s)); cudaFreeHost(sl->hpinned); }
+    if (sl->gexec) { cudaGraphExecDestroy(sl->gexec); sl->gexec = nullptr; sl->graph_key.clear(); }
+    sl->hpinned = nullptr;
+    sl->hcap = 0;
+    CK(cudaMallocHost(&sl->hpinned, hneed));
+    sl->hcap = hneed;
+  }
+  if (!sl->ev_start) CK(cudaEventCreate(&sl->ev_start));
+  if (!sl->ev_done) CK(cudaEventCreate(&sl->ev_done));
+  CK(cudaEventRecord(sl->ev_start, s));
+  int rc;
+  if (reuse_graph && sl->gexec && sl->graph_stream == s && same_batch(sl->graph_key, fr)) {
+    CK(cudaGraphLaunch(sl->gexec, s));
+    sl->prof_n = -1;
+    rc = LACOS_OK;
+  } else if (reuse_graph) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue(c, *sl, fr, L, s, false);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != LACOS_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (sl->gexec) cudaGraphExecDestroy(sl->gexec);
+    sl->gexec = nullptr;
+    e = cudaGraphInstantiate(&sl->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    sl->graph_key = fr;
+    sl->graph_stream = s;
+    sl->prof_n = -1;
+    CK(cudaGraphLaunch(sl->gexec, s));
+  } else {
+    rc = enqueue(c, *sl, fr, L, s, c->profiling);
+    if (rc != LACOS_OK) return rc;
+  }
+  CK(cudaEventRecord(sl->ev_done, s));
+  sl->busy = true;
+  sl->nframes = (int)fr.size();
+  sl->npix.resize(fr.size());
+  for (size_t i = 0; i < fr.size(); ++i) sl->npix[i] = (long long)fr[i].ny * fr[i].nx;
+  sl->per_frame = per_frame;
+  sl->ticket = c->next_ticket++;
+  *ticket = sl->ticket;
+  return LACOS_OK;
+}
+
+static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, sl.ev_start, sl.ev_done);
+  const FrameState* hs = (const FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * sl.nframes));
+  lacos_result agg{LACOS_OK, 0, 0, (double)ms};
+  if (sl.prof_n >= 0) {
+    lacos_profile& P = c->last_prof;
+    std::memset(&P, 0, sizeof(P));
+    P.n_detect = sl.prof_n;
+    for (int k = 1; k <= sl.prof_n; ++k)
+      cudaEventElapsedTime(&P.detect_ms[k - 1], sl.prof_ev[k - 1], sl.prof_ev[k]);
+    cudaEventElapsedTime(&P.finalize_ms, sl.prof_ev[sl.prof_n], sl.prof_ev[sl.prof_n + 1]);
+    for (int i = 0; i < sl.nframes; ++i) {
+      P.px_iterations += sl.npix[i] * hs[i].iters_run;
+      P.n_sprime += (long long)hs[i].n_sprime;
+      P.n_fine += (long long)hs[i].n_fine;
+      P.n_replace += (long long)hs[i].n_replace;
+    }
+  }
+  for (int i = 0; i < sl.nframes; ++i) {
+    lacos_result r{LACOS_OK, hs[i].iters_run, (long long)hs[i].flagged, (double)ms};
+    if (hs[i].err & ERR_NONFINITE) r.status = LACOS_ENONFINITE;
+    else if (hs[i].err & ERR_TIMEOUT) r.status = LACOS_ETIMEOUT;
+    if (sl.per_frame) sl.per_frame[i] = r;
+    if (agg.status == LACOS_OK) agg.status = r.status;
+    agg.iters_run = std::max(agg.iters_run, r.iters_run);
+    agg.n_flagged += r.n_flagged;
+  }
+  if (res) *res = agg;
+  sl.busy = false;
+  sl.per_frame = nullptr;
+  return LACOS_OK;
+}
+
+extern "C" {
+
+const char* lacos_version(void) { return "lacos-gb300 0.1 (sm_103a)"; }
+
+size_t lacos_scratch_bytes(int ny, int nx) {
+  if (ny < 1 || nx < 1) return 0;
+  std::vector<FrameReq> fr(1);
+  fr[0].ny = ny;
+  fr[0].nx = nx;
+  return layout_for(fr).total;
+}
+
+int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_slots) {
+  if (!out || device < 0 || max_slots < 0) return LACOS_EINVAL;
+  *out = nullptr;
+  lacos_ctx* c = new lacos_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t(8) << 30);
+  c->slots.resize(max_slots ? max_slots : 64);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_detect, detect_kernel, NT, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, NT, 0);
+  if (e != cudaSuccess) {
+    delete c;
+    return LACOS_ECUDA;
+  }
+  c->blocks_per_sm_detect = std::max(1, c->blocks_per_sm_detect);
+  c->blocks_per_sm_final = std::max(1, c->blocks_per_sm_final);
+  *out = c;
+  return LACOS_OK;
+}
+
+int lacos_submit(lacos_ctx* c, const void* d_frame, lacos_dtype dt, int ny, int nx,
+                 const lacos_params* p, uint8_t* d_mask, float* d_clean, lacos_stream stream,
+                 unsigned long long* ticket) {
+  if (!p) return LACOS_EINVAL;
+  std::vector<FrameReq> fr{{d_frame, (int)dt, ny, nx, *p, d_mask, d_clean}};
+  return submit_impl(c, fr, (cudaStream_t)stream, 0, nullptr, ticket);
+}
+
+int lacos_submit_batch(lacos_ctx* c, int n, const void* const* d_frames, const int* dtypes,
+                       const int* ny, const int* nx, const lacos_params* params,
+                       uint8_t* const* d_masks, float* const* d_cleans, lacos_stream stream,
+                       int reuse_graph, lacos_result* per_frame, unsigned long long* ticket) {
+  if (n < 1 || !d_frames || !dtypes || !ny || !nx || !params || !d_masks || !d_cleans)
+    return LACOS_EINVAL;
+  std::vector<FrameReq> fr((size_t)n);
+  for (int i = 0; i < n; ++i)
+    fr[i] = {d_frames[i], dtypes[i], ny[i], nx[i], params[i], d_masks[i], d_cleans[i]};
+  return submit_impl(c, fr, (cudaStream_t)stream, reuse_graph, per_frame, ticket);
+}
+
+int lacos_poll(lacos_ctx* c, unsigned long long ticket, lacos_result* res) {
+  if (!c) return LACOS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (auto& sl : c->slots) {
+    if (!sl.busy || sl.ticket != ticket) continue;
+    cudaError_t e = cudaEventQuery(sl.ev_done);
+    if (e == cudaErrorNotReady) return LACOS_PENDING;
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return finish(c, sl, res);
+  }
+  return LACOS_EUNKNOWN_TICKET;
+}
+
+int lacos_wait(lacos_ctx* c, unsigned long long ticket, lacos_result* res) {
+  if (!c) return LACOS_EINVAL;
+  cudaEvent_t ev = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto& sl : c->slots)
+      if (sl.busy && sl.ticket == ticket) ev = sl.ev_done;
+  }
+  if (!ev) return LACOS_EUNKNOWN_TICKET;
+  cudaError_t e = cudaEventSynchronize(ev);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  return lacos_poll(c, ticket, res);
+}
+
+int lacos_last_cuda_error(lacos_ctx* c) { return c ? c->last_cuda.load() : 0; }
+
+int lacos_set_profiling(lacos_ctx* c, int on) {
+  if (!c) return LACOS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->profiling = on != 0;
+  return LACOS_OK;
+}
+
+int lacos_last_profile(lacos_ctx* c, lacos_profile* out) {
+  if (!c || !out) return LACOS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->last_prof;
+  return LACOS_OK;
+}
+
+int lacos_destroy(lacos_ctx* c) {
+  if (!c) return LACOS_EINVAL;
+  cudaSetDevice(c->device);
+  int rc = LACOS_OK;
+  for (auto& sl : c->slots) {
+    if (sl.ev_done && cudaEventSynchronize(sl.ev_done) != cudaSuccess) rc = LACOS_ECUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = LACOS_ECUDA;
+  for (auto& sl : c->slots) {
+    if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+    if (sl.dscratch) cudaFree(sl.dscratch);
+    if (sl.hpinned) cudaFreeHost(sl.hpinned);
+    if (sl.ev_start) cudaEventDestroy(sl.ev_start);
+    if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+    for (cudaEvent_t e : sl.prof_ev) cudaEventDestroy(e);
+  }
+  delete c;
+  return rc;
+}
+
+}  // extern "C"

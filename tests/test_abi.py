@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every entry point include/lacos.h declares (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    out = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            out |= set(re.findall(r"\b(lacos_\w+)\s*\(", text))
+    return out
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_17938_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert {"lacos_create", "lacos_submit", "lacos_poll", "lacos_destroy"} <= syms
+    for s in sorted(syms):
+        assert hasattr(lib, s), s
+
+
+def test_host_only_entry_points(lib):
+    lib.lacos_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.lacos_version()
+    lib.lacos_scratch_bytes.restype = ctypes.c_size_t
+    lib.lacos_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    n = lib.lacos_scratch_bytes(6388, 9576)
+    # two bit-packed mask buffers dominate: 2 * 6388 * ceil(9576/32) * 4 bytes
+    assert 2 * 6388 * 300 * 4 <= n < 2 * 6388 * 300 * 4 + (1 << 20)
+    assert lib.lacos_scratch_bytes(0, 5) == 0
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    lib.lacos_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
+    assert lib.lacos_create(None, 0, 0, 0) == -1
+    lib.lacos_poll.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p]
+    assert lib.lacos_poll(None, 1, None) == -1
+    lib.lacos_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.lacos_destroy(None) == -1
+
+
+def test_networks_header_matches_generator_and_verifies():
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2602_17938_gb300", "csrc", "gen_networks.py")
+    spec = importlib.util.spec_from_file_location("gen_networks", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    nets = gen.build_all()
+    assert gen.verify(nets, trials=300)
+    text = open(os.path.join(ROOT, "paper_2602_17938_gb300", "csrc", "networks.cuh")).read()
+    for name, (dag, outs, shape, doc) in nets.items():
+        assert gen.emit_function(name, dag, outs, shape, doc) in text, name

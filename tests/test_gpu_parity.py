@@ -1,0 +1,227 @@
+"""GPU (CUDA path, through the C ABI) vs the float32 CPU oracle: bit-exact.
+
+The masks are compared byte for byte and the cleaned frames bit for bit;
+iters_run and n_flagged must match too.  Full-size frames are checked on
+sampled crops the oracle can finish in seconds (a crop with a 64-pixel
+margin reproduces the frame's result in its interior: one iteration reads
+at most 8 pixels away), plus properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_17938_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_17938_gb300 import build, lacos
+    build.build()
+    c = lacos.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(ctx, frame, gain, rn, **kw):
+    from paper_2602_17938_gb300 import lacos
+    mask, clean, res = lacos.clean_frame(lacos.to_device(frame), gain, rn, ctx=ctx, **kw)
+    torch.cuda.synchronize()
+    return mask.cpu().numpy(), clean.cpu().numpy(), res
+
+
+def assert_same(frame, gain, rn, gpu, **kw):
+    m, c, res = gpu
+    m_ref, c_ref, it_ref, nf_ref = oracle.run(frame, gain, rn, **kw)
+    bad = np.argwhere(m != m_ref)
+    assert bad.size == 0, f"{len(bad)} mask px differ, first at {bad[:5].tolist()}"
+    badc = np.argwhere(c.view(np.uint32) != c_ref.view(np.uint32))
+    assert badc.size == 0, f"{len(badc)} cleaned px differ, first at {badc[:5].tolist()}"
+    assert res.status == 0
+    assert res.iters_run == it_ref and res.n_flagged == nf_ref
+    return m_ref, c_ref
+
+
+def noisy_with_hits(ny, nx, seed, sky=100.0, gain=1.0, rn=1.5, n_hits=None, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    sig = math.sqrt(gain * sky + rn * rn) / gain
+    f = sky + sig * rng.standard_normal((ny, nx))
+    n_hits = max(1, ny * nx // 150) if n_hits is None else n_hits
+    ys, xs = rng.integers(0, ny, n_hits), rng.integers(0, nx, n_hits)
+    f[ys, xs] += rng.uniform(200, 3000, n_hits)
+    if dtype == np.uint16:
+        return np.clip(np.rint(f), 0, 65535).astype(np.uint16)
+    return f.astype(np.float32)
+
+
+def test_config0_bit_exact(ctx):
+    spec = synth.config_specs(0)[0]
+    f = synth.make_frame(spec)
+    assert_same(f, spec.gain, spec.readnoise, gpu_run(ctx, f, spec.gain, spec.readnoise))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (37, 1), (2, 2), (7, 7), (13, 9), (31, 33),
+                                   (32, 32), (33, 65), (64, 64), (95, 129), (100, 37)])
+def test_small_and_ragged_frames(ctx, shape):
+    f = noisy_with_hits(*shape, seed=shape[0] * 1000 + shape[1])
+    assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5))
+
+
+@pytest.mark.parametrize("shape", [(300, 433), (129, 64)])
+def test_uint16_salt_and_pepper(ctx, shape):
+    spec = synth.FrameSpec(shape[0], shape[1], "u16", (11, shape[0]), sky=300.0, gain=0.8,
+                           readnoise=1.2, n_stars=10, n_tracks=150, hot_frac=0.005, salt_pepper=True)
+    f = synth.make_frame(spec)
+    assert_same(f, spec.gain, spec.readnoise, gpu_run(ctx, f, spec.gain, spec.readnoise))
+
+
+@pytest.mark.parametrize("niter", [0, 1, 2, 6])
+def test_niter_values(ctx, niter):
+    f = noisy_with_hits(150, 170, seed=3)
+    assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5, niter=niter), niter=niter)
+
+
+def test_unnormalised_fine_structure_variant(ctx):
+    f = noisy_with_hits(120, 140, seed=4)
+    assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5, fine_norm=False), fnorm=False)
+
+
+def test_negative_values_and_negative_zero(ctx):
+    f = noisy_with_hits(90, 110, seed=5, sky=0.0)
+    f[::7, ::5] = -0.0
+    f[3, 3] = -500.0
+    assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5))
+
+
+def test_saturation(ctx):
+    f = noisy_with_hits(96, 96, seed=6)
+    f[20:23, 30:33] = 65535.0
+    f[50, 50] = 65535.0
+    for sat in (65535.0, 0.0, 3000.0):
+        assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5, satlevel=sat), satlevel=sat)
+
+
+def test_dense_hits_exercise_widened_replacement(ctx):
+    # A 15x15 block of rough bright texture (uniform 0-20000 ADU added per
+    # pixel) is flagged almost entirely, leaving 5x5 windows with no
+    # unflagged member, so the replacement widens to 7x7 and beyond.
+    for seed in (3, 11, 27):
+        rng = np.random.default_rng(seed)
+        f = (100 + 10 * rng.standard_normal((80, 90))).astype(np.float32)
+        f[30:45, 30:45] += rng.uniform(0, 20000, (15, 15)).astype(np.float32)
+        m_ref, _ = assert_same(f, 1.0, 1.5, gpu_run(ctx, f, 1.0, 1.5))
+        from numpy.lib.stride_tricks import sliding_window_view
+        full = sliding_window_view(np.pad(m_ref, 2, mode="edge"), (5, 5)).all(axis=(2, 3)) & (m_ref == 1)
+        assert full.any(), "test frame no longer reaches the widened replacement"
+
+
+def test_varied_parameters(ctx):
+    f = noisy_with_hits(140, 160, seed=8)
+    for kw in ({"sigclip": 3.0, "sigfrac": 0.5, "objlim": 2.0}, {"sigclip": 6.0, "sigfrac": 1.5, "objlim": 8.0},
+               {"sigclip": 4.5, "sigfrac": 0.1, "objlim": 0.5}):
+        assert_same(f, 2.5, 4.0, gpu_run(ctx, f, 2.5, 4.0, **kw), **kw)
+
+
+def test_nonfinite_input_reported(ctx):
+    f = noisy_with_hits(40, 40, seed=9)
+    f[5, 5] = np.nan
+    _, _, res = gpu_run(ctx, f, 1.0, 1.5)
+    from paper_2602_17938_gb300 import lacos
+    assert res.status == lacos.ENONFINITE
+
+
+def test_argument_errors(ctx):
+    from paper_2602_17938_gb300 import lacos
+    f = lacos.to_device(noisy_with_hits(16, 16, seed=1))
+    m = torch.empty((16, 16), dtype=torch.uint8, device="cuda")
+    c = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    for bad in (dict(gain=0.0), dict(gain=-1.0), dict(sigclip=0.0), dict(niter=-1), dict(niter=257),
+                dict(readnoise=-1.0), dict(objlim=float("nan"))):
+        kw = dict(gain=1.0, readnoise=1.5)
+        kw.update(bad)
+        with pytest.raises(lacos.LacosError) as e:
+            ctx.submit(f, lacos.make_params(**kw), m, c)
+        assert e.value.code == lacos.EINVAL
+    with pytest.raises(lacos.LacosError) as e:
+        ctx.poll(123456789)
+    assert e.value.code == lacos.EUNKNOWN_TICKET
+
+
+def test_budget_and_slots(ctx):
+    from paper_2602_17938_gb300 import lacos
+    f = lacos.to_device(noisy_with_hits(64, 64, seed=2))
+    m = torch.empty((64, 64), dtype=torch.uint8, device="cuda")
+    c = torch.empty((64, 64), dtype=torch.float32, device="cuda")
+    p = lacos.make_params(1.0, 1.5)
+    with lacos.Context(0, hbm_budget_bytes=1024, max_slots=1) as tiny:
+        with pytest.raises(lacos.LacosError) as e:
+            tiny.submit(f, p, m, c)
+        assert e.value.code == lacos.ENOMEM
+    with lacos.Context(0, max_slots=1) as one:
+        t = one.submit(f, p, m, c)
+        with pytest.raises(lacos.LacosError) as e:
+            one.submit(f, p, m, c)  # the only slot is held until polled
+        assert e.value.code == lacos.EAGAIN
+        r = one.wait(t)
+        assert r.status == 0
+        t2 = one.submit(f, p, m, c)
+        assert one.wait(t2).status == 0
+
+
+def test_batch_equals_single_frames(ctx):
+    from paper_2602_17938_gb300 import lacos
+    frames = [noisy_with_hits(70, 90, seed=20), noisy_with_hits(33, 200, seed=21),
+              noisy_with_hits(128, 64, seed=22, dtype=np.uint16), noisy_with_hits(5, 5, seed=23)]
+    niters = [4, 1, 6, 2]
+    gains = [1.0, 0.7, 1.3, 2.0]
+    dev = [lacos.to_device(x) for x in frames]
+    masks = [torch.empty(x.shape, dtype=torch.uint8, device="cuda") for x in frames]
+    cleans = [torch.empty(x.shape, dtype=torch.float32, device="cuda") for x in frames]
+    ps = [lacos.make_params(g, 1.5, niter=n) for g, n in zip(gains, niters)]
+    for reuse in (False, True, True):
+        t, per = ctx.submit_batch(dev, ps, masks, cleans, reuse_graph=reuse)
+        agg = ctx.wait(t)
+        torch.cuda.synchronize()
+        for i, x in enumerate(frames):
+            m_ref, c_ref, it_ref, nf_ref = oracle.run(x, gains[i], 1.5, niter=niters[i])
+            assert np.array_equal(masks[i].cpu().numpy(), m_ref)
+            assert np.array_equal(cleans[i].cpu().numpy().view(np.uint32), c_ref.view(np.uint32))
+            assert per[i].iters_run == it_ref and per[i].n_flagged == nf_ref
+        assert agg.n_flagged == sum(p.n_flagged for p in per)
+
+
+def _crop_check(frame, spec, mask, clean, boxes, margin=64):
+    ny, nx = frame.shape
+    for (y0, y1, x0, x1) in boxes:
+        cy0, cy1 = max(0, y0 - margin), min(ny, y1 + margin)
+        cx0, cx1 = max(0, x0 - margin), min(nx, x1 + margin)
+        crop = np.ascontiguousarray(frame[cy0:cy1, cx0:cx1])
+        m_ref, c_ref, _, _ = oracle.run(crop, spec.gain, spec.readnoise, niter=spec.niter)
+        sy, sx = slice(y0 - cy0, y1 - cy0), slice(x0 - cx0, x1 - cx0)
+        assert np.array_equal(mask[y0:y1, x0:x1], m_ref[sy, sx]), (y0, x0)
+        assert np.array_equal(clean[y0:y1, x0:x1].view(np.uint32), c_ref[sy, sx].view(np.uint32)), (y0, x0)
+
+
+def _sample_boxes(ny, nx, rng, n=10, size=48):
+    boxes = [(0, size, 0, size), (ny - size, ny, nx - size, nx), (0, size, nx - size, nx),
+             (ny - size, ny, 0, size)]
+    for _ in range(n):
+        y0, x0 = int(rng.integers(0, ny - size)), int(rng.integers(0, nx - size))
+        boxes.append((y0, y0 + size, x0, x0 + size))
+    return boxes
+
+
+def test_full_size_61mpx_uint16_sampled(ctx):
+    spec = synth.config_specs(1)[0]
+    f = synth.make_frame(spec)
+    m, c, res = gpu_run(ctx, f, spec.gain, spec.readnoise, niter=spec.niter)
+    assert res.status == 0 and res.n_flagged == int(m.sum()) > 0
+    np.testing.assert_array_equal(c[m == 0], f[m == 0].astype(np.float32))
+    _crop_check(f, spec, m, c, _sample_boxes(*f.shape, np.random.default_rng(1)))
