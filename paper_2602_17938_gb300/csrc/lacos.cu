@@ -2,11 +2,12 @@
 //
 // A context owns a fixed set of slots.  A submitted request (one frame or a
 // batch) takes a free slot, whose device scratch -- per-frame descriptors,
-// per-frame state, two bit-packed mask buffers per frame and the tile-queue
-// heads -- is allocated stream-ordered and charged against the context's
-// HBM budget.  The request's work is queued on the caller's stream:
+// per-frame state, two bit-packed mask buffers and three bit-planes per
+// frame, and the tile-queue heads -- is allocated stream-ordered and charged
+// against the context's HBM budget.  The request's work is queued on the
+// caller's stream:
 //   memcpy(descriptors) ; memset(state, heads, M_0) ;
-//   detect_kernel(k) for k = 1..max niter ; finalize_kernel ;
+//   { core_kernel(k) ; grow_kernel(k) } for k = 1..max niter ; finalize_kernel ;
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
 // Iteration control is on the device: an iteration whose predecessor
@@ -51,10 +52,11 @@ struct Slot {
   // CUDA graph of the last batch (replayed when the same batch comes back).
   cudaGraphExec_t gexec = nullptr;
   std::vector<FrameReq> graph_key;
-  cudaStream_t graph_stream = nullptr;
-  // Profiling events: [0] before the first detect, [k] after detect k, [n+1] after finalize.
+  cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be uncapturable)
+  // Profiling events: [0] before level 1, [2k-1] after core k, [2k] after grow k,
+  // [2n+1] after finalize.
   std::vector<cudaEvent_t> prof_ev;
-  int prof_n = -1;  // detect launches recorded for the request in flight (-1: none)
+  int prof_n = -1;  // levels recorded for the request in flight (-1: none)
   std::vector<long long> npix;
 };
 
@@ -87,7 +89,7 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 2 * maskbuf_bytes(f.ny, f.nx);
+    off += 5 * maskbuf_bytes(f.ny, f.nx);  // M buffers 0/1, planes sig/lo/cand
   }
   L.total = off;
   return L;
@@ -104,7 +106,7 @@ struct lacos_ctx {
   unsigned long long next_ticket = 1;
   std::atomic<int> last_cuda{0};
   int num_sms = 0;
-  int blocks_per_sm_detect = 1;
+  int blocks_per_sm_core = 1;
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
@@ -164,6 +166,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   // Host descriptors in the pinned buffer (states come back after them).
   FrameDesc* hdesc = (FrameDesc*)sl.hpinned;
   unsigned total = 0;
+  unsigned long long total_words = 0;
   int max_niter = 0;
   for (size_t i = 0; i < fr.size(); ++i) {
     const FrameReq& f = fr[i];
@@ -174,8 +177,12 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.ny = f.ny;
     h.nx = f.nx;
     h.wpr = wpr_of(f.nx);
+    const size_t mb = maskbuf_bytes(f.ny, f.nx);
     h.mbuf0 = (uint32_t*)(d + L.mask_off[i]);
-    h.mbuf1 = (uint32_t*)(d + L.mask_off[i] + maskbuf_bytes(f.ny, f.nx));
+    h.mbuf1 = (uint32_t*)(d + L.mask_off[i] + mb);
+    h.p_sig = (uint32_t*)(d + L.mask_off[i] + 2 * mb);
+    h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
+    h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -196,6 +203,8 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.tile_begin = total;
     total += tiles;
     h.tile_end = total;
+    h.word_begin = total_words;
+    total_words += (unsigned long long)f.ny * h.wpr;
     max_niter = std::max(max_niter, f.p.niter);
   }
   CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
@@ -204,9 +213,10 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   for (size_t i = 0; i < fr.size(); ++i)
     CK(cudaMemsetAsync(d + L.mask_off[i], 0, maskbuf_bytes(fr[i].ny, fr[i].nx), s));
   const int nf = (int)fr.size();
-  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_detect));
+  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core));
+  const unsigned gg = (unsigned)((total_words + NT - 1) / NT);
   if (prof) {
-    while ((int)sl.prof_ev.size() < max_niter + 2) {
+    while ((int)sl.prof_ev.size() < 2 * max_niter + 2) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
       sl.prof_ev.push_back(e);
@@ -214,14 +224,17 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     CK(cudaEventRecord(sl.prof_ev[0], s));
   }
   for (int k = 1; k <= max_niter; ++k) {
-    detect_kernel<<<gd, NT, 0, s>>>(ddesc, nf, total, k, heads + k);
+    core_kernel<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + k);
     CK(cudaGetLastError());
-    if (prof) CK(cudaEventRecord(sl.prof_ev[k], s));
+    if (prof) CK(cudaEventRecord(sl.prof_ev[2 * k - 1], s));
+    grow_kernel<<<gg, NT, 0, s>>>(ddesc, nf, total_words, k);
+    CK(cudaGetLastError());
+    if (prof) CK(cudaEventRecord(sl.prof_ev[2 * k], s));
   }
   const unsigned gf = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
   finalize_kernel<<<gf, NT, 0, s>>>(ddesc, nf, total, heads + LACOS_MAX_NITER + 1);
   CK(cudaGetLastError());
-  if (prof) CK(cudaEventRecord(sl.prof_ev[max_niter + 1], s));
+  if (prof) CK(cudaEventRecord(sl.prof_ev[2 * max_niter + 1], s));
   sl.prof_n = prof ? max_niter : -1;
   FrameState* hstate = (FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * fr.size()));
   CK(cudaMemcpyAsync(hstate, dstate, sizeof(FrameState) * fr.size(), cudaMemcpyDeviceToHost, s));
@@ -272,15 +285,17 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream
   if (!sl->ev_done) CK(cudaEventCreate(&sl->ev_done));
   CK(cudaEventRecord(sl->ev_start, s));
   int rc;
-  if (reuse_graph && sl->gexec && sl->graph_stream == s && same_batch(sl->graph_key, fr)) {
+  if (reuse_graph && sl->gexec && same_batch(sl->graph_key, fr)) {
     CK(cudaGraphLaunch(sl->gexec, s));
     sl->prof_n = -1;
     rc = LACOS_OK;
   } else if (reuse_graph) {
+    // Capture on the slot's own stream, then launch the graph on the caller's.
+    if (!sl->cap_stream) CK(cudaStreamCreateWithFlags(&sl->cap_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue(c, *sl, fr, L, s, false);
-    cudaError_t e = cudaStreamEndCapture(s, &g);
+    CK(cudaStreamBeginCapture(sl->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue(c, *sl, fr, L, sl->cap_stream, false);
+    cudaError_t e = cudaStreamEndCapture(sl->cap_stream, &g);
     if (rc != LACOS_OK) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_fail(c, e);
     if (sl->gexec) cudaGraphExecDestroy(sl->gexec);
@@ -289,7 +304,6 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c, e);
     sl->graph_key = fr;
-    sl->graph_stream = s;
     sl->prof_n = -1;
     CK(cudaGraphLaunch(sl->gexec, s));
   } else {
@@ -315,10 +329,12 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
   if (sl.prof_n >= 0) {
     lacos_profile& P = c->last_prof;
     std::memset(&P, 0, sizeof(P));
-    P.n_detect = sl.prof_n;
-    for (int k = 1; k <= sl.prof_n; ++k)
-      cudaEventElapsedTime(&P.detect_ms[k - 1], sl.prof_ev[k - 1], sl.prof_ev[k]);
-    cudaEventElapsedTime(&P.finalize_ms, sl.prof_ev[sl.prof_n], sl.prof_ev[sl.prof_n + 1]);
+    P.n_levels = sl.prof_n;
+    for (int k = 1; k <= sl.prof_n; ++k) {
+      cudaEventElapsedTime(&P.core_ms[k - 1], sl.prof_ev[2 * k - 2], sl.prof_ev[2 * k - 1]);
+      cudaEventElapsedTime(&P.grow_ms[k - 1], sl.prof_ev[2 * k - 1], sl.prof_ev[2 * k]);
+    }
+    cudaEventElapsedTime(&P.finalize_ms, sl.prof_ev[2 * sl.prof_n], sl.prof_ev[2 * sl.prof_n + 1]);
     for (int i = 0; i < sl.nframes; ++i) {
       P.px_iterations += sl.npix[i] * hs[i].iters_run;
       P.n_sprime += (long long)hs[i].n_sprime;
@@ -363,14 +379,18 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_detect, detect_kernel, NT, 0);
+    e = cudaFuncSetAttribute(core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(CoreSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core, core_kernel, NT,
+                                                      sizeof(CoreSmem));
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, NT, 0);
   if (e != cudaSuccess) {
     delete c;
     return LACOS_ECUDA;
   }
-  c->blocks_per_sm_detect = std::max(1, c->blocks_per_sm_detect);
+  c->blocks_per_sm_core = std::max(1, c->blocks_per_sm_core);
   c->blocks_per_sm_final = std::max(1, c->blocks_per_sm_final);
   *out = c;
   return LACOS_OK;
@@ -454,6 +474,7 @@ int lacos_destroy(lacos_ctx* c) {
     if (sl.ev_start) cudaEventDestroy(sl.ev_start);
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
     for (cudaEvent_t e : sl.prof_ev) cudaEventDestroy(e);
+    if (sl.cap_stream) cudaStreamDestroy(sl.cap_stream);
   }
   delete c;
   return rc;

@@ -1,18 +1,22 @@
 // Device code of the L.A.Cosmic detect-and-clean iteration (sm_103a).
 //
-// One iteration k is ONE kernel over a tile work queue.  A CTA takes an
-// output tile, stages the original frame X0 and the previous cumulative mask
-// M_{k-1} with an 8-pixel halo in shared memory, rebuilds the working image
-// I_{k-1} on the fly (unflagged pixels keep X0, flagged pixels take the
-// masked median of unflagged X0 -- step 7 of the previous iteration, which
-// depends only on X0 and M_{k-1}), then runs steps 1-6 on the tile and
-// writes M_k = M_{k-1} | g2 as packed bits.  A finalize kernel writes the
-// uint8 mask and the float32 cleaned frame from the last mask.
+// Iteration k is two kernels over the frame's tiles:
+//   core_kernel: a CTA takes a TH x TW output tile, stages the original
+//     frame X0 and the cumulative mask M_{k-1} with a 6-pixel halo in shared
+//     memory and rebuilds the working image I_{k-1} on the fly (unflagged
+//     pixels keep X0, flagged pixels take the masked median of unflagged X0:
+//     step 7 of the previous iteration depends only on X0 and M_{k-1}).  It
+//     then computes L+, N and S densely on the tile + 2, med3(I) on the
+//     tile + 3, and -- only where a threshold can still pass, from compacted
+//     lists -- S' = S - med5(S) and the fine-structure test, and writes three
+//     bit-planes for the tile: S' > sigclip, S' > sigfrac*sigclip (both
+//     excluding saturated pixels) and the candidates (steps 1-5).
+//   grow_kernel: word-parallel 3x3 dilations of the bit-planes (step 6),
+//     M_k = M_{k-1} | g2 and the count of newly flagged pixels.
+// finalize_kernel writes the uint8 mask and the float32 cleaned frame.
 //
-// Regions (relative to the tile): R8 staged X0/M, R6 working image,
-// R4 significance S, R2 S'/F/candidates, R1 first growth, R0 output.  Every
-// stage evaluates its own array only at in-frame positions and reads out-of-
-// frame neighbours at clamped coordinates (clamp-to-edge per stage).
+// Every stage evaluates its own array at in-frame positions only and reads
+// out-of-frame neighbours at clamped coordinates (clamp-to-edge per stage).
 //
 // Exactness: all float arithmetic uses the explicit round-to-nearest
 // intrinsics in the same operation order as the float32 CPU definition, the
@@ -40,9 +44,10 @@ __device__ __forceinline__ float MX(float a, float b) { return fmaxf(a, b); }
 namespace lacos {
 
 constexpr int TH = 32;   // output tile rows
-constexpr int TW = 32;   // output tile columns (one 32-bit mask word per row)
+constexpr int TW = 64;   // output tile columns (two 32-bit mask words per row)
+constexpr int TWW = TW / 32;
 constexpr int NT = 256;  // threads per CTA
-constexpr int HX = 8;    // staging halo
+constexpr int HX = 6;    // staging halo of the core kernel
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -61,13 +66,17 @@ struct FrameDesc {
   int ny, nx, wpr;  // wpr: 32-bit mask words per row
   uint32_t* mbuf0;  // M_k lives in buffer k & 1 (M_0 = zeros in buffer 0)
   uint32_t* mbuf1;
+  uint32_t* p_sig;   // bit-planes of the current iteration (ny x wpr words each)
+  uint32_t* p_lo;
+  uint32_t* p_cand;
   uint8_t* mask_out;
   float* clean_out;
   FrameState* st;
   float gain, rn2, satlevel, sigclip, lo, thr_min, objlim;
   int niter, fnorm;
   int tiles_x;
-  unsigned int tile_begin, tile_end;  // this frame's range in the flattened tile list
+  unsigned int tile_begin, tile_end;    // this frame's range in the flattened tile list
+  unsigned long long word_begin;        // this frame's range in the flattened word list
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -164,18 +173,6 @@ struct Reg {
   __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + H); }
 };
 
-struct TileSmem {
-  float X[Reg<8>::N];        // X0, then I_{k-1} on R6
-  uint8_t Mb[Reg<8>::N];     // M_{k-1}
-  float S[Reg<4>::N];        // S on R4
-  float N[Reg<2>::N];        // N on R2
-  float Sp[Reg<2>::N];       // S' on R2 (-inf where S <= min threshold)
-  uint8_t C[Reg<2>::N];      // candidates on R2
-  uint8_t G1[Reg<1>::N];     // first growth on R1
-  unsigned long long cnt;
-  unsigned n_sp, n_f, n_rep;
-};
-
 __device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsigned item) {
   int lo = 0, hi = nframes - 1;
   while (lo < hi) {
@@ -185,61 +182,133 @@ __device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsign
   return lo;
 }
 
-__device__ void detect_tile(const FrameDesc& f, int k, int tix, TileSmem& sm) {
+__device__ __forceinline__ int frame_of_word(const FrameDesc* fr, int nframes, unsigned long long w) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].word_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Warp-aggregated append of `val` to a shared list when `pred` holds.  All
+// 32 lanes of the warp must call it.
+__device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* lst, unsigned* cnt) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) lst[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+// Copies every out-of-frame position of region H of an array indexed with
+// Reg<ARH> from its clamped in-frame position (clamp-to-edge of that stage).
+template <int H, int ARH, class T>
+__device__ __forceinline__ void edge_fill(T* A, int oy, int ox, int ny, int nx) {
+  for (int i = threadIdx.x; i < Reg<H>::N; i += NT) {
+    const int ly = i / Reg<H>::W - H, lx = i % Reg<H>::W - H;
+    const int gy = oy + ly, gx = ox + lx;
+    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
+    const int cy = clampi(gy, 0, ny - 1) - oy, cx = clampi(gx, 0, nx - 1) - ox;
+    A[Reg<ARH>::idx(ly, lx)] = A[Reg<ARH>::idx(cy, cx)];
+  }
+}
+
+struct CoreSmem {
+  float X[Reg<6>::N];        // X0, then I_{k-1} on R4
+  uint8_t Mb[Reg<6>::N];     // M_{k-1}
+  float S[Reg<2>::N];        // S on R2
+  float M3[Reg<3>::N];       // med3(I) on R3
+  float SpL[TH * TW];        // S' of the entries of the S' list
+  uint16_t list[Reg<4>::N];  // compacted work list (R4 indices for replacement, R0 otherwise)
+  uint16_t list2[TH * TW];   // F list: indices into the S' list
+  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo, bit2: candidate
+  unsigned nlist, nlist2;
+  unsigned n_sp, n_f, n_rep;
+};
+
+__device__ __forceinline__ float med5_at(const float* A, int P, int c) {
+  float w[25];
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[a * 5 + b] = A[c + (a - 2) * P + (b - 2)];
+  float m;
+  med5x5<float>(w, &m);
+  return m;
+}
+
+__device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
+  const float gm = __fmul_rn(f.gain, m5);
+  const float e = gm < 1e-4f ? 1e-4f : gm;
+  return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
+}
+
+__device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   const int tid = threadIdx.x;
   const int oy = (tix / f.tiles_x) * TH;
   const int ox = (tix % f.tiles_x) * TW;
   const int ny = f.ny, nx = f.nx;
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
-  uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
   const bool edge = (oy - HX < 0) || (ox - HX < 0) || (oy + TH + HX > ny) || (ox + TW + HX > nx);
   bool bad = false;
 
-  // Stage X0 and M_{k-1} on R8 at clamped coordinates.
-  for (int i = tid; i < Reg<8>::N; i += NT) {
-    const int ly = i / Reg<8>::W - 8, lx = i % Reg<8>::W - 8;
+  // Stage X0 and M_{k-1} on R6 at clamped coordinates.
+  for (int i = tid; i < Reg<6>::N; i += NT) {
+    const int ly = i / Reg<6>::W - 6, lx = i % Reg<6>::W - 6;
     const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
     sm.X[i] = load_x0(f, gy, gx, bad);
     sm.Mb[i] = (uint8_t)mask_bit(Mp, f.wpr, gy, gx);
   }
-  if (tid == 0) { sm.cnt = 0; sm.n_sp = 0; sm.n_f = 0; sm.n_rep = 0; }
+  for (int i = tid; i < TH * TW; i += NT) sm.flags[i] = 0;
+  if (tid == 0) { sm.n_sp = 0; sm.n_f = 0; sm.n_rep = 0; sm.nlist = 0; sm.nlist2 = 0; }
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
 
-  // Step 7 of the previous iteration: I_{k-1} on R6 (flagged pixels only;
-  // reads touch unflagged pixels only, writes flagged ones, so in place).
+  // Step 7 of the previous iteration: I_{k-1} on R4 at flagged pixels (a
+  // compacted list; reads touch unflagged pixels only, so it is in place).
   if (k > 1) {
-    for (int i = tid; i < Reg<6>::N; i += NT) {
-      const int ly = i / Reg<6>::W - 6, lx = i % Reg<6>::W - 6;
-      const int gy = oy + ly, gx = ox + lx;
-      if (gy < 0 || gy >= ny || gx < 0 || gx >= nx) continue;
-      const int c = Reg<8>::idx(ly, lx);
-      if (!sm.Mb[c]) continue;
-      float v;
-      if (!maskmed5(sm.X, sm.Mb, Reg<8>::W, c, v)) v = maskmed_wide(f, Mp, gy, gx);
-      sm.X[c] = v;
-      atomicAdd(&sm.n_rep, 1u);
+    for (int b = 0; b < Reg<4>::N; b += NT) {
+      const int i = b + tid;
+      bool p = false;
+      int c = 0;
+      if (i < Reg<4>::N) {
+        const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
+        const int gy = oy + ly, gx = ox + lx;
+        c = Reg<6>::idx(ly, lx);
+        p = gy >= 0 && gy < ny && gx >= 0 && gx < nx && sm.Mb[c];
+      }
+      list_append(p, (uint16_t)c, sm.list, &sm.nlist);
     }
     __syncthreads();
-    if (edge) {
-      for (int i = tid; i < Reg<6>::N; i += NT) {
-        const int ly = i / Reg<6>::W - 6, lx = i % Reg<6>::W - 6;
-        const int gy = oy + ly, gx = ox + lx;
-        if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-        sm.X[Reg<8>::idx(ly, lx)] =
-            sm.X[Reg<8>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+    const unsigned n = sm.nlist;
+    for (unsigned j = tid; j < n; j += NT) {
+      const int c = sm.list[j];
+      float v;
+      if (!maskmed5(sm.X, sm.Mb, Reg<6>::W, c, v)) {
+        const int ly = c / Reg<6>::W - 6, lx = c % Reg<6>::W - 6;
+        v = maskmed_wide(f, Mp, oy + ly, ox + lx);
       }
+      sm.X[c] = v;
+    }
+    if (tid == 0) { sm.n_rep = n; sm.nlist = 0; }
+    __syncthreads();
+    if (edge) {
+      edge_fill<4, 6>(sm.X, oy, ox, ny, nx);
       __syncthreads();
     }
   }
 
-  // Steps 1-3: L+, noise, significance on R4.
-  for (int i = tid; i < Reg<4>::N; i += NT) {
-    const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
+  // Steps 1-3 (L+, noise, significance) on R2, and med3(I) on R3.
+  for (int i = tid; i < Reg<2>::N; i += NT) {
+    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
     const int gy = oy + ly, gx = ox + lx;
     if (gy < 0 || gy >= ny || gx < 0 || gx >= nx) continue;
-    const int c = Reg<8>::idx(ly, lx);
-    constexpr int P = Reg<8>::W;
+    const int c = Reg<6>::idx(ly, lx);
+    constexpr int P = Reg<6>::W;
     const float v = sm.X[c], u = sm.X[c - P], d = sm.X[c + P], l = sm.X[c - 1], r = sm.X[c + 1];
     const float vv = __fadd_rn(v, v);
     float c1 = __fsub_rn(__fsub_rn(vv, u), l);
@@ -251,156 +320,124 @@ __device__ void detect_tile(const FrameDesc& f, int k, int tix, TileSmem& sm) {
     c3 = c3 > 0.0f ? c3 : 0.0f;
     c4 = c4 > 0.0f ? c4 : 0.0f;
     const float L = __fmul_rn(__fadd_rn(__fadd_rn(c1, c2), __fadd_rn(c3, c4)), 0.25f);
-    float w[25];
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-      for (int b = 0; b < 5; ++b) w[a * 5 + b] = sm.X[c + (a - 2) * P + (b - 2)];
-    float m5;
-    med5x5<float>(w, &m5);
-    const float gm = __fmul_rn(f.gain, m5);
-    const float e = gm < 1e-4f ? 1e-4f : gm;
-    const float N = __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
+    const float N = noise_of(f, med5_at(sm.X, P, c));
     sm.S[i] = __fdiv_rn(L, __fadd_rn(N, N));
-    if (ly >= -2 && ly < TH + 2 && lx >= -2 && lx < TW + 2) sm.N[Reg<2>::idx(ly, lx)] = N;
+  }
+  for (int i = tid; i < Reg<3>::N; i += NT) {
+    const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
+    const int gy = oy + ly, gx = ox + lx;
+    if (gy < 0 || gy >= ny || gx < 0 || gx >= nx) continue;
+    const int c = Reg<6>::idx(ly, lx);
+    float w[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) w[a * 3 + b] = sm.X[c + (a - 1) * Reg<6>::W + (b - 1)];
+    float m;
+    med3x3<float>(w, &m);
+    sm.M3[i] = m;
   }
   __syncthreads();
   if (edge) {
-    for (int i = tid; i < Reg<4>::N; i += NT) {
-      const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
-      const int gy = oy + ly, gx = ox + lx;
-      if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-      sm.S[i] = sm.S[Reg<4>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
-    }
+    edge_fill<2, 2>(sm.S, oy, ox, ny, nx);
+    edge_fill<3, 3>(sm.M3, oy, ox, ny, nx);
     __syncthreads();
   }
 
-  // Large-structure removal S' = S - med5(S), only where S exceeds the lower
-  // threshold (S' <= S there otherwise, so every test on S' fails anyway).
-  for (int i = tid; i < Reg<2>::N; i += NT) {
-    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-    const int gy = oy + ly, gx = ox + lx;
-    float sp = lacos_net::neg_inf<float>();
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-      const int c = Reg<4>::idx(ly, lx);
-      const float s = sm.S[c];
-      if (s > f.thr_min) {
-        float w[25];
-#pragma unroll
-        for (int a = 0; a < 5; ++a)
-#pragma unroll
-          for (int b = 0; b < 5; ++b) w[a * 5 + b] = sm.S[c + (a - 2) * Reg<4>::W + (b - 2)];
-        float m;
-        med5x5<float>(w, &m);
-        sp = __fsub_rn(s, m);
-        atomicAdd(&sm.n_sp, 1u);
-      }
+  // S' = S - med5(S), only where S exceeds the lower threshold (elsewhere
+  // S' <= S fails every test): compacted list over the tile.
+  for (int b = 0; b < TH * TW; b += NT) {
+    const int i = b + tid;
+    const int ly = i / TW, lx = i % TW;
+    const bool p = (oy + ly) < ny && (ox + lx) < nx && sm.S[Reg<2>::idx(ly, lx)] > f.thr_min;
+    list_append(p, (uint16_t)i, sm.list, &sm.nlist);
+  }
+  __syncthreads();
+  {
+    const unsigned n = sm.nlist;
+    for (unsigned j = tid; j < n; j += NT) {
+      const int i = sm.list[j];
+      const int ly = i / TW, lx = i % TW;
+      const int c = Reg<2>::idx(ly, lx);
+      const float sp = __fsub_rn(sm.S[c], med5_at(sm.S, Reg<2>::W, c));
+      sm.SpL[j] = sp;
+      const int c6 = Reg<6>::idx(ly, lx);
+      const bool sat = f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel;
+      const bool sig = !sat && sp > f.sigclip;
+      sm.flags[i] = (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
     }
-    sm.Sp[i] = sp;
+    if (tid == 0) sm.n_sp = n;
   }
   __syncthreads();
 
-  // Steps 4-5: candidates (sigclip on S', objlim on S'/F), F only where needed.
-  for (int i = tid; i < Reg<2>::N; i += NT) {
-    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-    const int gy = oy + ly, gx = ox + lx;
-    uint8_t cand = 0;
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-      const int c8 = Reg<8>::idx(ly, lx);
-      const bool sat = f.satlevel > 0.0f && !sm.Mb[c8] && sm.X[c8] >= f.satlevel;
-      const float sp = sm.Sp[i];
-      if (!sat && sp > f.sigclip) {
-        // med3 at the 7x7 clamped neighbourhood, then med7 of those.
-        float m3w[49];
-        float m3p = 0.0f;
-        for (int a = 0; a < 7; ++a) {
-          const int qy = clampi(gy + a - 3, 0, ny - 1) - oy;
-          for (int b = 0; b < 7; ++b) {
-            const int qx = clampi(gx + b - 3, 0, nx - 1) - ox;
-            const int q = Reg<8>::idx(qy, qx);
-            float w[9];
-#pragma unroll
-            for (int e = 0; e < 3; ++e)
-#pragma unroll
-              for (int g = 0; g < 3; ++g) w[e * 3 + g] = sm.X[q + (e - 1) * Reg<8>::W + (g - 1)];
-            float m;
-            med3x3<float>(w, &m);
-            m3w[a * 7 + b] = m;
-            if (a == 3 && b == 3) m3p = m;
-          }
-        }
-        float m7;
-        med7x7<float>(m3w, &m7);
-        const float diff = __fsub_rn(m3p, m7);
-        float F = f.fnorm ? __fdiv_rn(diff, sm.N[i]) : diff;
-        F = F < 0.01f ? 0.01f : F;
-        cand = __fdiv_rn(sp, F) > f.objlim ? 1 : 0;
-        atomicAdd(&sm.n_f, 1u);
-      }
+  // Steps 4-5: the fine-structure test where S' > sigclip (not saturated).
+  {
+    const unsigned n = sm.nlist;
+    for (unsigned b = 0; b < n; b += NT) {
+      const unsigned j = b + tid;
+      const bool p = j < n && (sm.flags[sm.list[j]] & 1);
+      list_append(p, (uint16_t)j, sm.list2, &sm.nlist2);
     }
-    sm.C[i] = cand;
+  }
+  __syncthreads();
+  {
+    const unsigned n = sm.nlist2;
+    for (unsigned t = tid; t < n; t += NT) {
+      const int j = sm.list2[t];
+      const int i = sm.list[j];
+      const int ly = i / TW, lx = i % TW;
+      const int c3 = Reg<3>::idx(ly, lx);
+      float w[49];
+#pragma unroll
+      for (int a = 0; a < 7; ++a)
+#pragma unroll
+        for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
+      float m7;
+      med7x7<float>(w, &m7);
+      const float diff = __fsub_rn(sm.M3[c3], m7);
+      float F = diff;
+      if (f.fnorm) F = __fdiv_rn(diff, noise_of(f, med5_at(sm.X, Reg<6>::W, Reg<6>::idx(ly, lx))));
+      F = F < 0.01f ? 0.01f : F;
+      if (__fdiv_rn(sm.SpL[j], F) > f.objlim) sm.flags[i] |= 4;
+    }
+    if (tid == 0) sm.n_f = n;
   }
   __syncthreads();
 
-  // Step 6a: g1 = dil3(cand) & S' > sigclip & !sat on R1.
-  for (int i = tid; i < Reg<1>::N; i += NT) {
-    const int ly = i / Reg<1>::W - 1, lx = i % Reg<1>::W - 1;
-    const int gy = oy + ly, gx = ox + lx;
-    uint8_t g = 0;
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-      const int c2 = Reg<2>::idx(ly, lx);
-      const int c8 = Reg<8>::idx(ly, lx);
-      const bool sat = f.satlevel > 0.0f && !sm.Mb[c8] && sm.X[c8] >= f.satlevel;
-      uint8_t d = 0;
-#pragma unroll
-      for (int a = -1; a <= 1; ++a)
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) d |= sm.C[c2 + a * Reg<2>::W + b];  // C = 0 off-frame
-      g = (d && sm.Sp[c2] > f.sigclip && !sat) ? 1 : 0;
-    }
-    sm.G1[i] = g;
-  }
-  __syncthreads();
-
-  // Step 6b: g2 = dil3(g1) & S' > sigfrac*sigclip & !sat; M_k = M_{k-1} | g2.
+  // Bit-planes of the tile (bits beyond the frame stay 0).
   const int lane = tid & 31, warp = tid >> 5;
-  unsigned long long fresh = 0;
-  for (int ly = warp; ly < TH; ly += NT / 32) {
-    const int lx = lane;
-    const int gy = oy + ly, gx = ox + lx;
-    const bool in = gy < ny && gx < nx;
-    const int c8 = Reg<8>::idx(ly, lx);
-    bool g2 = false, mprev = false;
-    if (in) {
-      const int c1 = Reg<1>::idx(ly, lx);
-      const int c2 = Reg<2>::idx(ly, lx);
-      const bool sat = f.satlevel > 0.0f && !sm.Mb[c8] && sm.X[c8] >= f.satlevel;
-      uint8_t d = 0;
-#pragma unroll
-      for (int a = -1; a <= 1; ++a)
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) d |= sm.G1[c1 + a * Reg<1>::W + b];
-      g2 = d && sm.Sp[c2] > f.lo && !sat;
-      mprev = sm.Mb[c8] != 0;
+  for (int r = warp; r < TH * TWW; r += NT / 32) {
+    const int ly = r / TWW, wd = r % TWW;
+    const int lx = wd * 32 + lane;
+    const int gy = oy + ly;
+    const uint8_t fl = ((ox + lx) < nx && gy < ny) ? sm.flags[ly * TW + lx] : 0;
+    const unsigned sig = __ballot_sync(0xffffffffu, fl & 1);
+    const unsigned lo = __ballot_sync(0xffffffffu, fl & 2);
+    const unsigned cand = __ballot_sync(0xffffffffu, fl & 4);
+    const int w = (ox >> 5) + wd;
+    if (lane == 0 && gy < ny && w < f.wpr) {
+      const size_t q = (size_t)gy * f.wpr + w;
+      f.p_sig[q] = sig;
+      f.p_lo[q] = lo;
+      f.p_cand[q] = cand;
     }
-    const unsigned word = __ballot_sync(0xffffffffu, g2 || mprev);
-    const unsigned nw = __ballot_sync(0xffffffffu, g2 && !mprev);
-    if (lane == 0 && gy < ny) Mn[(size_t)gy * f.wpr + (ox >> 5)] = word;
-    fresh += __popc(nw);
   }
-  if (lane == 0 && fresh) atomicAdd(&sm.cnt, fresh);
-  __syncthreads();
   if (tid == 0) {
-    if (sm.cnt) atomicAdd(&f.st->fresh[k], sm.cnt);
     if (sm.n_sp) atomicAdd(&f.st->n_sprime, (unsigned long long)sm.n_sp);
     if (sm.n_f) atomicAdd(&f.st->n_fine, (unsigned long long)sm.n_f);
     if (sm.n_rep) atomicAdd(&f.st->n_replace, (unsigned long long)sm.n_rep);
   }
 }
 
-__global__ void __launch_bounds__(NT) detect_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                    unsigned total, int k, unsigned* head) {
-  __shared__ TileSmem sm;
+__device__ __forceinline__ bool iteration_runs(const FrameDesc& f, int k) {
+  if (k > f.niter) return false;
+  return k == 1 || *(volatile unsigned long long*)&f.st->fresh[k - 1] != 0;
+}
+
+__global__ void __launch_bounds__(NT) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                  unsigned total, int k, unsigned* head) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CoreSmem& sm = *reinterpret_cast<CoreSmem*>(smem_raw);
   __shared__ unsigned s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(head, 1u);
@@ -408,12 +445,82 @@ __global__ void __launch_bounds__(NT) detect_kernel(const FrameDesc* __restrict_
     const unsigned item = s_item;
     __syncthreads();
     if (item >= total) break;
-    const int fi = frame_of(fr, nframes, item);
-    const FrameDesc& f = fr[fi];
-    if (k > f.niter) continue;
-    if (k > 1 && *(volatile unsigned long long*)&f.st->fresh[k - 1] == 0) continue;
-    detect_tile(f, k, (int)(item - f.tile_begin), sm);
+    const FrameDesc& f = fr[frame_of(fr, nframes, item)];
+    if (!iteration_runs(f, k)) continue;
+    core_tile(f, k, (int)(item - f.tile_begin), sm);
     __syncthreads();
+  }
+}
+
+// Step 6 on 32-pixel words: one thread per word of M_k.  The horizontal
+// 3-dilation of a word takes the edge bits of its neighbours.
+__device__ __forceinline__ uint32_t plane_word(const uint32_t* P, int ny, int wpr, int y, int w) {
+  if (y < 0 || y >= ny || w < 0 || w >= wpr) return 0u;
+  return __ldg(P + (size_t)y * wpr + w);
+}
+
+__device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
+  return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
+}
+
+__global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                  unsigned long long total_words, int k) {
+  const unsigned long long gw = (unsigned long long)blockIdx.x * NT + threadIdx.x;
+  unsigned cnt = 0;
+  int fi = -1;
+  if (gw < total_words) {
+    fi = frame_of_word(fr, nframes, gw);
+    const FrameDesc& f = fr[fi];
+    if (iteration_runs(f, k)) {
+      const unsigned long long q = gw - f.word_begin;
+      const int y = (int)(q / (unsigned)f.wpr), w = (int)(q % (unsigned)f.wpr);
+      const int ny = f.ny, wpr = f.wpr;
+      // Dilated candidates on rows y-1..y+1 for words w-1..w+1.
+      uint32_t dc[3][3];
+      uint32_t cand[5][5];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) cand[a][b] = plane_word(f.p_cand, ny, wpr, y - 2 + a, w - 2 + b);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) v |= hdil(cand[r + a][b], cand[r + a][b + 1], cand[r + a][b + 2]);
+          dc[r][b] = v;
+        }
+      // g1 = dil3(cand) & sig on rows y-1..y+1, words w-1..w+1; the edge words
+      // are exact where g2 of word w reads them (their inner edge bit).
+      uint32_t g1[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) g1[r][b] = dc[r][b] & plane_word(f.p_sig, ny, wpr, y - 1 + r, w - 1 + b);
+      uint32_t d2 = 0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) d2 |= hdil(g1[r][0], g1[r][1], g1[r][2]);
+      const uint32_t g2 = d2 & plane_word(f.p_lo, ny, wpr, y, w);
+      const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
+      uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
+      const uint32_t mp = __ldg(Mp + (size_t)y * wpr + w);
+      Mn[(size_t)y * wpr + w] = mp | g2;
+      cnt = __popc(g2 & ~mp);
+    }
+  }
+  // Per-warp reduction; lanes may belong to different frames at a frame
+  // boundary, so each lane with a count adds it (rare) unless the warp agrees.
+  const int lane = threadIdx.x & 31;
+  const int f0 = __shfl_sync(0xffffffffu, fi, 0);
+  const bool same = __all_sync(0xffffffffu, fi == f0);
+  if (same) {
+    unsigned s = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && s && f0 >= 0) atomicAdd(&fr[f0].st->fresh[k], (unsigned long long)s);
+  } else if (cnt) {
+    atomicAdd(&fr[fi].st->fresh[k], (unsigned long long)cnt);
   }
 }
 

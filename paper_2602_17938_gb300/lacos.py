@@ -38,7 +38,8 @@ class Params(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("n_detect", ctypes.c_int), ("detect_ms", ctypes.c_float * MAX_NITER),
+    _fields_ = [("n_levels", ctypes.c_int), ("core_ms", ctypes.c_float * MAX_NITER),
+                ("grow_ms", ctypes.c_float * MAX_NITER),
                 ("finalize_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
                 ("n_sprime", ctypes.c_longlong), ("n_fine", ctypes.c_longlong),
                 ("n_replace", ctypes.c_longlong)]
@@ -181,7 +182,8 @@ class Context:
         rc = self.lib.lacos_last_profile(self.h, ctypes.byref(p))
         if rc != OK:
             raise LacosError(rc, "lacos_last_profile")
-        return {"detect_ms": list(p.detect_ms[:p.n_detect]), "finalize_ms": p.finalize_ms,
+        return {"core_ms": list(p.core_ms[:p.n_levels]), "grow_ms": list(p.grow_ms[:p.n_levels]),
+                "finalize_ms": p.finalize_ms,
                 "px_iterations": p.px_iterations, "n_sprime": p.n_sprime, "n_fine": p.n_fine,
                 "n_replace": p.n_replace}
 

@@ -38,8 +38,9 @@ def test_host_only_entry_points(lib):
     lib.lacos_scratch_bytes.restype = ctypes.c_size_t
     lib.lacos_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
     n = lib.lacos_scratch_bytes(6388, 9576)
-    # two bit-packed mask buffers dominate: 2 * 6388 * ceil(9576/32) * 4 bytes
-    assert 2 * 6388 * 300 * 4 <= n < 2 * 6388 * 300 * 4 + (1 << 20)
+    # five bit-planes (two mask buffers, three test planes) dominate:
+    # 5 * 6388 * ceil(9576/32) * 4 bytes
+    assert 5 * 6388 * 300 * 4 <= n < 5 * 6388 * 300 * 4 + (1 << 20)
     assert lib.lacos_scratch_bytes(0, 5) == 0
 
 
