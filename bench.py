@@ -224,19 +224,17 @@ def run_ours(args):
     ctx.set_profiling(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    tickets = []
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
+        profs = []
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            tickets.append(ctx.submit(d_frame, params, d_mask, d_clean))
+            t = ctx.submit(d_frame, params, d_mask, d_clean)
             ev[i][1].record(stream)
-        profs = []
-        for t in tickets:
-            r = ctx.wait(t)
+            ctx.wait(t)
             profs.append(ctx.last_profile())
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -252,16 +250,16 @@ def run_ours(args):
 
     # Roofline of the dominant kernel (core), from the live per-launch profile.
     det_ms = [ms for p in profs for ms in p["core_ms"]]
-    grow_ms = [ms for p in profs for ms in p["grow_ms"]]
-    fin_ms = [p["finalize_ms"] for p in profs]
+    per_kernel = {name: sum(ms for p in profs for ms in p[name + "_ms"])
+                  for name in ("core", "fine", "grow")}
+    per_kernel["final"] = sum(p["final_ms"] for p in profs)
     n_launch = len(det_ms)
     ops = sum(netcost.detect_minmax_ops(p) for p in profs)
     det_avg_ms = sum(det_ms) / max(1, n_launch)
     achieved = ops / n_launch / (det_avg_ms * 1e-3) / 1e12 if n_launch else None
     peak_f32, peak_u16 = alu_peak()
     peak = peak_f32 / 1e3 if peak_f32 else None
-    share = sum(det_ms) / (sum(det_ms) + sum(grow_ms) + sum(fin_ms))
-
+    share = per_kernel["core"] / sum(per_kernel.values())
     # End to end through the public API: pinned host frame in, mask+cleaned out.
     h_frame = torch.from_numpy(frame.view(np.int16)).pin_memory().view(torch.uint16)
     h_mask = torch.empty((ny, nx), dtype=torch.uint8).pin_memory()
@@ -299,16 +297,15 @@ def run_ours(args):
                      "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
                      "kernel": "core_kernel", "peak_source": "measured min.f32/max.f32 issue rate",
                      "avg_launch_ms": det_avg_ms, "launch_share": share,
-                     "grow_avg_ms": sum(grow_ms) / max(1, len(grow_ms)),
-                     "finalize_avg_ms": sum(fin_ms) / max(1, len(fin_ms))},
+                     "kernel_ms_per_step": {k: v / len(profs) for k, v in per_kernel.items()}},
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": 2 * npix,
                 "d2h_bytes_per_step": 5 * npix},
-        "gpu_launches": args.steps * (2 * spec.niter + 1),
+        "gpu_launches": args.steps * (3 * spec.niter + 1),
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
         "check_clean_equals_input_outside_mask": ok_check,
         "alu_peak_gops": {"f32": peak_f32, "u16x2": peak_u16},
-        "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_fine", "n_replace")},
+        "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_fine", "n_replace", "n_replace_wide")},
     }
     if cpu:
         line["cpu_baseline"] = cpu

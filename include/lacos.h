@@ -26,7 +26,7 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (5 bits per pixel plus a few kilobytes per request),
+ * its scratch (12.6 bytes per pixel plus a few kilobytes per request),
  * charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
@@ -125,13 +125,15 @@ int lacos_submit_batch(lacos_ctx *c, int n, const void *const *d_frames, const i
  * its stream, so requests replayed from a CUDA graph are not profiled). */
 typedef struct {
   int n_levels;                        /* iteration levels launched */
-  float core_ms[LACOS_MAX_NITER];      /* device time of each level's core (steps 1-5) launch */
-  float grow_ms[LACOS_MAX_NITER];      /* device time of each level's growth (step 6) launch */
-  float finalize_ms;                   /* device time of the finalize launch */
+  float core_ms[LACOS_MAX_NITER];      /* per level: step 7 of the previous level, steps 1-4 */
+  float fine_ms[LACOS_MAX_NITER];      /* per level: step 5 (fine structure, objlim) */
+  float grow_ms[LACOS_MAX_NITER];      /* per level: step 6 (growth, mask update) */
+  float final_ms;                      /* cleaned frame (last step 7) and uint8 mask */
   long long px_iterations;             /* sum over frames of ny*nx*iters_run */
   long long n_sprime;                  /* pixels where S' = S - med5(S) was evaluated */
   long long n_fine;                    /* pixels where the fine-structure F was evaluated */
   long long n_replace;                 /* masked-median replacements inside core launches */
+  long long n_replace_wide;            /* ... of which the 5x5 window was fully flagged */
 } lacos_profile;
 
 int lacos_set_profiling(lacos_ctx *c, int on);

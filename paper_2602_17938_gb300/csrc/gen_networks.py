@@ -270,35 +270,158 @@ def emit_function(name, dag, outputs, in_shape, doc):
     return "\n".join(lines)
 
 
+def block_median(K, W, R):
+    """K x K medians of a W-wide, R-tall block of outputs sharing work.
+
+    Inputs are v[(R+K-1) x (W+K-1)] (row-major); outputs o[R x W].  Each
+    input column is sorted once per output row with vertical sharing (the
+    rows common to all R windows are sorted once and the remaining rows
+    merged in, halving recursively), created lazily left to right so the
+    emitted code streams across the block.  Per output row the K sorted
+    columns of a window are then combined:
+      K = 3: the 3x3 median is med3(max of column minima, med3 of column
+             medians, min of column maxima) (Paeth's construction), with the
+             pairwise max/min terms shared between neighbouring outputs;
+      K = 5: columns are merged in pairs shared by neighbouring output pairs,
+             the two pairs merged (only the ranks that can be the median are
+             kept by pruning) and the rank-12 element of that list and the
+             fifth column taken with ``select2``.
+    """
+    d = Dag()
+    ncol, nrow = W + K - 1, R + K - 1
+    inp = [[d.inp((r, c)) for c in range(ncol)] for r in range(nrow)]
+    colcache = {}
+
+    def colsort(c, y):
+        """Sorted column c over rows y..y+K-1, shared across the R rows."""
+        if (c, y) not in colcache:
+            def rec(lo, hi, core, core_rows):
+                if hi - lo == 1:
+                    extra = sorted(set(range(lo, lo + K)) - core_rows)
+                    colcache[(c, lo)] = d.merge(core, d.sortk([inp[e][c] for e in extra])
+                                                if len(extra) in (3, 5) else
+                                                d.sort([inp[e][c] for e in extra]))
+                    return
+                mid = (lo + hi) // 2
+                for a, b in ((lo, mid), (mid, hi)):
+                    rows = set(range(b - 1, a + K))
+                    extra = sorted(rows - core_rows)
+                    rec(a, b, d.merge(core, d.sort([inp[e][c] for e in extra])), rows)
+            rows = set(range(R - 1, K))
+            core = d.sort([inp[e][c] for e in sorted(rows)]) if rows else []
+            rec(0, R, core, rows)
+        return colcache[(c, y)]
+
+    M = (K * K - 1) // 2
+    outs = [[None] * W for _ in range(R)]
+    for x in range(W):
+        for y in range(R):
+            cols = [colsort(x + j, y) for j in range(K)]
+            if K == 3:
+                lo = [cc[0] for cc in cols]
+                me = [cc[1] for cc in cols]
+                hi = [cc[2] for cc in cols]
+                # pair terms at even x are shared with x+1: max(lo1, lo2) etc.
+                if x % 2 == 0:
+                    a = d.mx(d.mx(lo[1], lo[2]), lo[0])
+                    b = d.mn(d.mn(hi[1], hi[2]), hi[0])
+                else:
+                    a = d.mx(d.mx(lo[0], lo[1]), lo[2])
+                    b = d.mn(d.mn(hi[0], hi[1]), hi[2])
+                m = d.mx(d.mn(me[0], me[1]), d.mn(d.mx(me[0], me[1]), me[2]))
+                outs[y][x] = d.mx(d.mn(a, m), d.mn(d.mx(a, m), b))
+            elif K == 5:
+                if x % 2 == 0:
+                    q = d.merge(d.merge(cols[1], cols[2]), d.merge(cols[3], cols[4]))
+                    outs[y][x] = d.select2(q, cols[0], M)
+                else:
+                    q = d.merge(d.merge(cols[0], cols[1]), d.merge(cols[2], cols[3]))
+                    outs[y][x] = d.select2(q, cols[4], M)
+            else:
+                outs[y][x] = d.select_rank(cols, M)
+    return d, [outs[y][x] for y in range(R) for x in range(W)]
+
+
+BLOCKS = {"blk_med5_4x2": (5, 4, 2), "blk_med3_8x2": (3, 8, 2)}
+
+
 def build_all():
     nets = {}
     nets["med3x3"] = window_median(3) + ((3, 3), "Median of a 3x3 window, v row-major.")
     nets["med5x5"] = window_median(5) + ((5, 5), "Median of a 5x5 window, v row-major.")
     nets["med7x7"] = window_median(7) + ((7, 7), "Median of a 7x7 window, v row-major.")
+    for name, (K, W, R) in BLOCKS.items():
+        d, o = block_median(K, W, R)
+        nets[name] = (d, o, (R + K - 1, W + K - 1),
+                      f"{K}x{K} medians of a {W}x{R} block (W x R); v is "
+                      f"{R + K - 1}x{W + K - 1} row-major, o is {R}x{W} row-major.")
     return nets
 
 
-def verify(nets=None, trials=2000, seed=1):
-    """Check every network against a full sort (random keys with ties, 0-1 keys)."""
+def block_window(name, out_index):
+    """Input labels (row, col) of the window behind output ``out_index`` of a block."""
+    K, W, R = BLOCKS[name]
+    y, x = divmod(out_index, W)
+    return [(y + a, x + b) for a in range(K) for b in range(K)]
+
+
+def _windows(name, dag, outs):
+    labels = [nm[1] for nm in dag.names if nm[0] == "in"]
+    if name in BLOCKS:
+        return [block_window(name, j) for j in range(len(outs))]
+    return [labels]
+
+
+def verify(nets=None, trials=2000, seed=1, exhaustive=True, max_exhaustive_outputs=None):
+    """Check every network against a full sort of each output's window:
+    random keys with many ties, and (for windows of up to 25 keys) every
+    0-1 input of the window, bit-sliced with numpy (min = AND, max = OR),
+    which by the 0-1 principle covers all inputs of a comparator network."""
     nets = nets or build_all()
     rng = random.Random(seed)
     for name, (dag, outs, shape, _) in nets.items():
         labels = [nm[1] for nm in dag.names if nm[0] == "in"]
-        n = len(labels)
+        wins = _windows(name, dag, outs)
         for t in range(trials):
             hi = [1, 3, 1000][t % 3]
-            vals = [rng.randint(0, hi) for _ in labels]
-            env = dict(zip(labels, vals))
-            got = evaluate(dag, outs, env)[0]
-            exp = sorted(vals)[(n - 1) // 2]
-            if got != exp:
-                raise AssertionError(f"{name}: got {got}, expected {exp} for {vals}")
-        if n <= 20:
-            for bits in itertools.product((0, 1), repeat=n):
-                env = dict(zip(labels, bits))
-                if evaluate(dag, outs, env)[0] != sorted(bits)[(n - 1) // 2]:
-                    raise AssertionError(f"{name}: 0-1 failure")
+            env = {lab: rng.randint(0, hi) for lab in labels}
+            got = evaluate(dag, outs, env)
+            for j, win in enumerate(wins):
+                vals = sorted(env[lab] for lab in win)
+                if got[j] != vals[(len(vals) - 1) // 2]:
+                    raise AssertionError(f"{name}: output {j} wrong on {env}")
+        if exhaustive:
+            for j, win in enumerate(wins[:max_exhaustive_outputs]):
+                if len(win) <= 25:
+                    _exhaustive01(dag, outs[j], win, labels)
     return True
+
+
+def _exhaustive01(dag, out, win, labels):
+    import numpy as np
+    n = len(win)
+    total = 1 << n
+    idx = np.arange(total, dtype=np.uint64)
+    val = {}
+    inwin = {lab: k for k, lab in enumerate(win)}
+    for i, nm in enumerate(dag.names):
+        if nm[0] == "in":
+            k = inwin.get(nm[1])
+            val[i] = ((idx >> np.uint64(k)) & np.uint64(1)).astype(bool) if k is not None else None
+    for i in live_ops(dag, [out]):
+        kind, a, b = dag.names[i]
+        va = {NEG: False, POS: True}.get(a) if not isinstance(a, int) else val[a]
+        vb = {NEG: False, POS: True}.get(b) if not isinstance(b, int) else val[b]
+        if va is None or vb is None:
+            raise AssertionError("output depends on an input outside its window")
+        val[i] = (va & vb) if kind == "min" else (va | vb)
+    ones = np.zeros(total, dtype=np.int64)
+    for k in range(n):
+        ones += ((idx >> np.uint64(k)) & np.uint64(1)).astype(np.int64)
+    expect = ones >= (n + 1) // 2  # the median of n (odd) 0/1 keys is 1 iff #ones > n/2
+    got = val[out] if isinstance(out, int) else np.full(total, out == POS)
+    if not np.array_equal(np.asarray(got, dtype=bool), expect):
+        raise AssertionError("0-1 exhaustive check failed")
 
 
 HEADER = """// Generated by gen_networks.py -- do not edit.
@@ -310,7 +433,7 @@ HEADER = """// Generated by gen_networks.py -- do not edit.
 
 def main(out_path):
     nets = build_all()
-    verify(nets, trials=500)
+    verify(nets, trials=300)
     parts = [HEADER]
     for name, (dag, outs, shape, doc) in nets.items():
         parts.append(emit_function(name, dag, outs, shape, doc))
@@ -318,7 +441,7 @@ def main(out_path):
     with open(out_path, "w") as f:
         f.write(text)
     for name, (dag, outs, shape, doc) in nets.items():
-        print(f"{name}: {count_ops(dag, outs)} ops")
+        print(f"{name}: {count_ops(dag, outs)} ops, {count_ops(dag, outs) / len(outs):.1f} per output")
 
 
 if __name__ == "__main__":

@@ -7,7 +7,8 @@
 // against the context's HBM budget.  The request's work is queued on the
 // caller's stream:
 //   memcpy(descriptors) ; memset(state, heads, M_0) ;
-//   { core_kernel(k) ; grow_kernel(k) } for k = 1..max niter ; finalize_kernel ;
+//   { core_kernel(k) ; fine_kernel(k) ; grow_kernel(k) } for k = 1..max niter ;
+//   finalize_kernel ;
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
 // Iteration control is on the device: an iteration whose predecessor
@@ -18,6 +19,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -29,6 +31,10 @@ using namespace lacos;
 namespace {
 
 constexpr size_t kAlign = 256;
+// Tile-queue heads: one per (kernel, level) plus the final replace.
+constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
+constexpr int kHeadCore = 0, kHeadFine = kHeadLevels;
+constexpr int kHeadFinal = 2 * kHeadLevels, kHeads = 2 * kHeadLevels + 1;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 struct FrameReq {
@@ -53,8 +59,7 @@ struct Slot {
   cudaGraphExec_t gexec = nullptr;
   std::vector<FrameReq> graph_key;
   cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be uncapturable)
-  // Profiling events: [0] before level 1, [2k-1] after core k, [2k] after grow k,
-  // [2n+1] after finalize.
+  // Profiling events (see enqueue).
   std::vector<cudaEvent_t> prof_ev;
   int prof_n = -1;  // levels recorded for the request in flight (-1: none)
   std::vector<long long> npix;
@@ -73,6 +78,7 @@ bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) 
 
 int wpr_of(int nx) { return (nx + 31) / 32; }
 size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
+size_t plane_bytes(int ny, int nx) { return align_up((size_t)ny * nx * sizeof(float)); }
 
 struct Layout {
   size_t heads, descs, states, masks, total;
@@ -83,13 +89,13 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   Layout L;
   const size_t n = fr.size();
   L.heads = 0;
-  L.descs = align_up(sizeof(unsigned) * (LACOS_MAX_NITER + 2));
+  L.descs = align_up(sizeof(unsigned) * kHeads);
   L.states = L.descs + align_up(sizeof(FrameDesc) * n);
   L.masks = L.states + align_up(sizeof(FrameState) * n);
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 5 * maskbuf_bytes(f.ny, f.nx);  // M buffers 0/1, planes sig/lo/cand
+    off += 5 * maskbuf_bytes(f.ny, f.nx) + 3 * plane_bytes(f.ny, f.nx);  // M 0/1, sig/lo/cand, S', med3, N
   }
   L.total = off;
   return L;
@@ -106,11 +112,18 @@ struct lacos_ctx {
   unsigned long long next_ticket = 1;
   std::atomic<int> last_cuda{0};
   int num_sms = 0;
+  int core_variant = 3;                 // index into kCoreVariants
+  int blocks_per_sm_core_v[4] = {1, 1, 1, 1};
   int blocks_per_sm_core = 1;
+  int blocks_per_sm_fine = 1;
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
 };
+
+using CoreFn = void (*)(const FrameDesc*, int, unsigned, int, unsigned*);
+// Core-kernel variants: register allocation bounded for 1, 2, 3 or 4 CTAs/SM.
+static const CoreFn kCoreVariants[4] = {core_kernel<1>, core_kernel<2>, core_kernel<3>, core_kernel<4>};
 
 static int cuda_fail(lacos_ctx* c, cudaError_t e) {
   if (c) c->last_cuda = (int)e;
@@ -183,6 +196,9 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_sig = (uint32_t*)(d + L.mask_off[i] + 2 * mb);
     h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
+    h.sp = (float*)(d + L.mask_off[i] + 5 * mb);
+    h.m3 = (float*)(d + L.mask_off[i] + 5 * mb + plane_bytes(f.ny, f.nx));
+    h.np = (float*)(d + L.mask_off[i] + 5 * mb + 2 * plane_bytes(f.ny, f.nx));
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -208,33 +224,45 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     max_niter = std::max(max_niter, f.p.niter);
   }
   CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(heads, 0, sizeof(unsigned) * (LACOS_MAX_NITER + 2), s));
+  CK(cudaMemsetAsync(heads, 0, sizeof(unsigned) * kHeads, s));
   CK(cudaMemsetAsync(dstate, 0, sizeof(FrameState) * fr.size(), s));
   for (size_t i = 0; i < fr.size(); ++i)
     CK(cudaMemsetAsync(d + L.mask_off[i], 0, maskbuf_bytes(fr[i].ny, fr[i].nx), s));
   const int nf = (int)fr.size();
-  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core));
-  const unsigned gg = (unsigned)((total_words + NT - 1) / NT);
+  const int cv = c->core_variant;
+  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core_v[cv]));
+  const unsigned gfn = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_fine));
+  const unsigned gfi = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
+  const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
+  // Profile events: [0] start, level k: [3k-2] after core, [3k-1] after
+  // fine, [3k] after grow, [3n+1] after finalize.
+  const int nev = 3 * max_niter + 2;
   if (prof) {
-    while ((int)sl.prof_ev.size() < 2 * max_niter + 2) {
+    while ((int)sl.prof_ev.size() < nev) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
       sl.prof_ev.push_back(e);
     }
     CK(cudaEventRecord(sl.prof_ev[0], s));
   }
+  auto mark = [&](int i) -> int {
+    if (prof) CK(cudaEventRecord(sl.prof_ev[i], s));
+    return LACOS_OK;
+  };
   for (int k = 1; k <= max_niter; ++k) {
-    core_kernel<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + k);
+    kCoreVariants[cv]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
     CK(cudaGetLastError());
-    if (prof) CK(cudaEventRecord(sl.prof_ev[2 * k - 1], s));
-    grow_kernel<<<gg, NT, 0, s>>>(ddesc, nf, total_words, k);
+    if (int rc = mark(3 * k - 2)) return rc;
+    fine_kernel<<<gfn, NT, 0, s>>>(ddesc, nf, total, k, heads + kHeadFine + k);
     CK(cudaGetLastError());
-    if (prof) CK(cudaEventRecord(sl.prof_ev[2 * k], s));
+    if (int rc = mark(3 * k - 1)) return rc;
+    grow_kernel<<<gw, NT, 0, s>>>(ddesc, nf, total_words, k);
+    CK(cudaGetLastError());
+    if (int rc = mark(3 * k)) return rc;
   }
-  const unsigned gf = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
-  finalize_kernel<<<gf, NT, 0, s>>>(ddesc, nf, total, heads + LACOS_MAX_NITER + 1);
+  finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, nf, total, heads + kHeadFinal);
   CK(cudaGetLastError());
-  if (prof) CK(cudaEventRecord(sl.prof_ev[2 * max_niter + 1], s));
+  if (int rc = mark(3 * max_niter + 1)) return rc;
   sl.prof_n = prof ? max_niter : -1;
   FrameState* hstate = (FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * fr.size()));
   CK(cudaMemcpyAsync(hstate, dstate, sizeof(FrameState) * fr.size(), cudaMemcpyDeviceToHost, s));
@@ -330,16 +358,19 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
     lacos_profile& P = c->last_prof;
     std::memset(&P, 0, sizeof(P));
     P.n_levels = sl.prof_n;
+    const auto& E = sl.prof_ev;
     for (int k = 1; k <= sl.prof_n; ++k) {
-      cudaEventElapsedTime(&P.core_ms[k - 1], sl.prof_ev[2 * k - 2], sl.prof_ev[2 * k - 1]);
-      cudaEventElapsedTime(&P.grow_ms[k - 1], sl.prof_ev[2 * k - 1], sl.prof_ev[2 * k]);
+      cudaEventElapsedTime(&P.core_ms[k - 1], E[3 * k - 3], E[3 * k - 2]);
+      cudaEventElapsedTime(&P.fine_ms[k - 1], E[3 * k - 2], E[3 * k - 1]);
+      cudaEventElapsedTime(&P.grow_ms[k - 1], E[3 * k - 1], E[3 * k]);
     }
-    cudaEventElapsedTime(&P.finalize_ms, sl.prof_ev[2 * sl.prof_n], sl.prof_ev[2 * sl.prof_n + 1]);
+    cudaEventElapsedTime(&P.final_ms, E[3 * sl.prof_n], E[3 * sl.prof_n + 1]);
     for (int i = 0; i < sl.nframes; ++i) {
       P.px_iterations += sl.npix[i] * hs[i].iters_run;
       P.n_sprime += (long long)hs[i].n_sprime;
       P.n_fine += (long long)hs[i].n_fine;
       P.n_replace += (long long)hs[i].n_replace;
+      P.n_replace_wide += (long long)hs[i].n_replace_wide;
     }
   }
   for (int i = 0; i < sl.nframes; ++i) {
@@ -378,20 +409,28 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   c->slots.resize(max_slots ? max_slots : 64);
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+    e = cudaFuncSetAttribute(kCoreVariants[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(CoreSmem));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core, core_kernel, NT,
-                                                      sizeof(CoreSmem));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[v], kCoreVariants[v],
+                                                        NT, sizeof(CoreSmem));
+    c->blocks_per_sm_core_v[v] = std::max(1, c->blocks_per_sm_core_v[v]);
+  }
+  if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
+    const int v = std::atoi(env);
+    if (v >= 0 && v < 4) c->core_variant = v;
+  }
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, NT, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_fine, fine_kernel, NT, 0);
   if (e != cudaSuccess) {
     delete c;
     return LACOS_ECUDA;
   }
-  c->blocks_per_sm_core = std::max(1, c->blocks_per_sm_core);
   c->blocks_per_sm_final = std::max(1, c->blocks_per_sm_final);
+  c->blocks_per_sm_fine = std::max(1, c->blocks_per_sm_fine);
   *out = c;
   return LACOS_OK;
 }

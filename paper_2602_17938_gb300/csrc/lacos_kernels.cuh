@@ -1,19 +1,22 @@
 // Device code of the L.A.Cosmic detect-and-clean iteration (sm_103a).
 //
-// Iteration k is two kernels over the frame's tiles:
-//   core_kernel: a CTA takes a TH x TW output tile, stages the original
-//     frame X0 and the cumulative mask M_{k-1} with a 6-pixel halo in shared
-//     memory and rebuilds the working image I_{k-1} on the fly (unflagged
-//     pixels keep X0, flagged pixels take the masked median of unflagged X0:
-//     step 7 of the previous iteration depends only on X0 and M_{k-1}).  It
-//     then computes L+, N and S densely on the tile + 2, med3(I) on the
-//     tile + 3, and -- only where a threshold can still pass, from compacted
-//     lists -- S' = S - med5(S) and the fine-structure test, and writes three
-//     bit-planes for the tile: S' > sigclip, S' > sigfrac*sigclip (both
-//     excluding saturated pixels) and the candidates (steps 1-5).
-//   grow_kernel: word-parallel 3x3 dilations of the bit-planes (step 6),
-//     M_k = M_{k-1} | g2 and the count of newly flagged pixels.
-// finalize_kernel writes the uint8 mask and the float32 cleaned frame.
+// Iteration k is three kernels:
+//   core_kernel: per TH x TW tile, stages the original frame X0 and the
+//     cumulative mask M_{k-1} with a 6-pixel halo and rebuilds the working
+//     image I_{k-1} = R(X0, M_{k-1}) on the tile + 4 (step 7 of the previous
+//     iteration: unflagged pixels keep X0, flagged ones take the masked
+//     median of unflagged X0, so I depends only on X0 and the mask); then
+//     L+, N and S densely on the tile + 2 and med3(I) on the tile (register
+//     blocks of shared min/max networks) and S' = S - med5(S) from a
+//     compacted list of the pixels where S exceeds the lower threshold
+//     (steps 1-4).  It writes the bit-planes S' > sigclip and S' >
+//     sigfrac*sigclip (both excluding saturated pixels), S' and N where S'
+//     exceeds sigclip, and the med3 plane;
+//   fine_kernel: step 5 at the set bits of the sigclip plane: F from the
+//     med3 plane, the objlim test, the candidate bit-plane;
+//   grow_kernel: step 6 on 32-pixel words, M_k = M_{k-1} | g2 and the count
+//     of newly flagged pixels.
+// finalize_kernel writes the cleaned frame R(X0, M) and the uint8 mask.
 //
 // Every stage evaluates its own array at in-frame positions only and reads
 // out-of-frame neighbours at clamped coordinates (clamp-to-edge per stage).
@@ -47,7 +50,6 @@ constexpr int TH = 32;   // output tile rows
 constexpr int TW = 64;   // output tile columns (two 32-bit mask words per row)
 constexpr int TWW = TW / 32;
 constexpr int NT = 256;  // threads per CTA
-constexpr int HX = 6;    // staging halo of the core kernel
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -56,6 +58,7 @@ struct FrameState {
   unsigned long long fresh[LACOS_MAX_NITER + 1];  // new pixels found by iteration k
   unsigned long long flagged;                      // pixels in the final mask
   unsigned long long n_sprime, n_fine, n_replace;  // sparse-work counters (profiling)
+  unsigned long long n_replace_wide;               // replacements whose 5x5 window was all flagged
   unsigned int err;
   int iters_run;
 };
@@ -69,8 +72,11 @@ struct FrameDesc {
   uint32_t* p_sig;   // bit-planes of the current iteration (ny x wpr words each)
   uint32_t* p_lo;
   uint32_t* p_cand;
+  float* sp;         // S' plane (written where S' > sigclip)
+  float* m3;         // med3(I) plane
+  float* np;         // N plane (written where S' > sigclip)
   uint8_t* mask_out;
-  float* clean_out;
+  float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
   float gain, rn2, satlevel, sigclip, lo, thr_min, objlim;
   int niter, fnorm;
@@ -102,13 +108,14 @@ __device__ __forceinline__ float from_okey(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Masked median with the window widened beyond 5x5 (rare: every pixel of
-// the 5x5 window is flagged).  Reads X0 and the mask from global memory and
-// selects the lower median by a 32-pass radix select on order keys.
-__device__ float maskmed_wide(const FrameDesc& f, const uint32_t* M, int gy, int gx) {
+// Masked median with the window widened to (2*r0+1)^2 and beyond (rare: the
+// smaller windows are fully flagged).  Reads X0 and the mask from global
+// memory and selects the lower median by a 32-pass radix select on order
+// keys.
+__device__ float maskmed_wide(const FrameDesc& f, const uint32_t* M, int gy, int gx, int r0) {
   const int rmax = max(f.ny, f.nx) + 2;
   bool bad = false;
-  for (int r = 3; r <= rmax; ++r) {
+  for (int r = r0; r <= rmax; ++r) {
     unsigned n = 0;
     for (int dy = -r; dy <= r; ++dy) {
       const int y = clampi(gy + dy, 0, f.ny - 1);
@@ -134,6 +141,58 @@ __device__ float maskmed_wide(const FrameDesc& f, const uint32_t* M, int gy, int
     return from_okey(prefix);
   }
   return load_x0(f, gy, gx, bad);  // unreachable: a frame always keeps an unflagged pixel
+}
+
+
+template <int H>
+struct Reg {
+  static constexpr int W = TW + 2 * H;
+  static constexpr int Hh = TH + 2 * H;
+  static constexpr int N = W * Hh;
+  __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + H); }
+};
+
+__device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsigned item) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int frame_of_word(const FrameDesc* fr, int nframes, unsigned long long w) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].word_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool iteration_runs(const FrameDesc& f, int k) {
+  if (k > f.niter) return false;
+  return k == 1 || *(volatile unsigned long long*)&f.st->fresh[k - 1] != 0;
+}
+
+// Iteration count actually executed (early stop included).
+__device__ __forceinline__ int run_of(const FrameDesc& f) {
+  for (int k = 1; k <= f.niter; ++k)
+    if (f.st->fresh[k] == 0) return k;
+  return f.niter;
+}
+
+// Warp-aggregated append of `val` to a shared list when `pred` holds.  All
+// 32 lanes of the warp must call it.
+__device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* lst, unsigned* cnt) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) lst[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
 // Masked 5x5 median at shared-memory index c of X (pitch P) with flags Mb:
@@ -165,80 +224,68 @@ __device__ __forceinline__ bool maskmed5(const float* X, const uint8_t* Mb, int 
   return true;
 }
 
-template <int H>
-struct Reg {
-  static constexpr int W = TW + 2 * H;
-  static constexpr int Hh = TH + 2 * H;
-  static constexpr int N = W * Hh;
-  __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + H); }
-};
-
-__device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsigned item) {
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (fr[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+// Masked 7x7 median (the first widening): the same sentinel scheme with the
+// rank-24 element of 49.  Returns false when no member is unflagged.
+__device__ __forceinline__ bool maskmed7(const float* X, const uint8_t* Mb, int P, int c, float& out) {
+  int n = 0;
+#pragma unroll
+  for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) n += Mb[c + dy * P + dx] ? 0 : 1;
+  if (n == 0) return false;
+  const int plo = 24 - (n - 1) / 2;
+  float v[49];
+  int seen = 0;
+#pragma unroll
+  for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) {
+      const int q = c + dy * P + dx;
+      const bool fl = Mb[q] != 0;
+      const float s = (seen < plo) ? lacos_net::neg_inf<float>() : lacos_net::pos_inf<float>();
+      seen += fl ? 1 : 0;
+      v[(dy + 3) * 7 + dx + 3] = fl ? s : X[q];
+    }
+  med7x7<float>(v, &out);
+  return true;
 }
 
-__device__ __forceinline__ int frame_of_word(const FrameDesc* fr, int nframes, unsigned long long w) {
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (fr[mid].word_begin <= w) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
+// ---- core: steps 1-4 on a tile --------------------------------------------
 
-// Warp-aggregated append of `val` to a shared list when `pred` holds.  All
-// 32 lanes of the warp must call it.
-__device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* lst, unsigned* cnt) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) lst[base + __popc(m & ((1u << lane) - 1u))] = val;
-}
-
-// Copies every out-of-frame position of region H of an array indexed with
-// Reg<ARH> from its clamped in-frame position (clamp-to-edge of that stage).
-template <int H, int ARH, class T>
-__device__ __forceinline__ void edge_fill(T* A, int oy, int ox, int ny, int nx) {
-  for (int i = threadIdx.x; i < Reg<H>::N; i += NT) {
-    const int ly = i / Reg<H>::W - H, lx = i % Reg<H>::W - H;
-    const int gy = oy + ly, gx = ox + lx;
-    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-    const int cy = clampi(gy, 0, ny - 1) - oy, cx = clampi(gx, 0, nx - 1) - ox;
-    A[Reg<ARH>::idx(ly, lx)] = A[Reg<ARH>::idx(cy, cx)];
-  }
-}
+constexpr int MWORDS = (TW + 12 + 31) / 32 + 1;  // mask words spanning R6 columns
 
 struct CoreSmem {
-  float X[Reg<6>::N];        // X0, then I_{k-1} on R4
-  uint8_t Mb[Reg<6>::N];     // M_{k-1}
+  float X[Reg<6>::N];        // X0 on R6, then the working image I_{k-1} on R4
+  uint8_t Mb[Reg<6>::N];     // M_{k-1} on R6
+  uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
   float S[Reg<2>::N];        // S on R2
-  float M3[Reg<3>::N];       // med3(I) on R3
-  float SpL[TH * TW];        // S' of the entries of the S' list
-  uint16_t list[Reg<4>::N];  // compacted work list (R4 indices for replacement, R0 otherwise)
-  uint16_t list2[TH * TW];   // F list: indices into the S' list
-  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo, bit2: candidate
-  unsigned nlist, nlist2;
-  unsigned n_sp, n_f, n_rep;
+  float N[TH * TW];          // N on the tile
+  uint16_t list[Reg<4>::N];  // work lists (replacement on R4, then S' on the tile)
+  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo (both not saturated)
+  unsigned nlist;
 };
 
-__device__ __forceinline__ float med5_at(const float* A, int P, int c) {
-  float w[25];
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) w[a * 5 + b] = A[c + (a - 2) * P + (b - 2)];
-  float m;
-  med5x5<float>(w, &m);
-  return m;
+// Stages X0 and the mask M (clamped coordinates) on region H of a tile:
+// X (Reg<H>-indexed floats), Mb (bytes), via the mask words of the rows.
+template <int H>
+__device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t* M, int oy, int ox,
+                                              float* X, uint8_t* Mb, uint32_t (*Mw)[MWORDS],
+                                              bool& bad) {
+  const int ny = f.ny, nx = f.nx;
+  const int w0 = clampi(ox - H, 0, nx - 1) >> 5;
+  for (int i = threadIdx.x; i < (TH + 2 * H) * MWORDS; i += NT) {
+    const int r = i / MWORDS, w = w0 + i % MWORDS;
+    const int gy = clampi(oy - H + r, 0, ny - 1);
+    Mw[r][i % MWORDS] = w < f.wpr ? __ldg(M + (size_t)gy * f.wpr + w) : 0u;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int i = threadIdx.x; i < Reg<H>::N; i += NT) {
+    const int ly = i / Reg<H>::W - H, lx = i % Reg<H>::W - H;
+    const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
+    X[i] = load_x0(f, gy, gx, bad);
+    Mb[i] = (uint8_t)((Mw[ly + H][(gx >> 5) - w0] >> (gx & 31)) & 1u);
+  }
 }
 
 __device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
@@ -247,29 +294,38 @@ __device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
   return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
 }
 
+__device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, float rt) {
+  const float vv = __fadd_rn(vc, vc);
+  float c1 = __fsub_rn(__fsub_rn(vv, up), lf);
+  float c2 = __fsub_rn(__fsub_rn(vv, up), rt);
+  float c3 = __fsub_rn(__fsub_rn(vv, dn), lf);
+  float c4 = __fsub_rn(__fsub_rn(vv, dn), rt);
+  c1 = c1 > 0.0f ? c1 : 0.0f;
+  c2 = c2 > 0.0f ? c2 : 0.0f;
+  c3 = c3 > 0.0f ? c3 : 0.0f;
+  c4 = c4 > 0.0f ? c4 : 0.0f;
+  return __fmul_rn(__fadd_rn(__fadd_rn(c1, c2), __fadd_rn(c3, c4)), 0.25f);
+}
+
 __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   const int tid = threadIdx.x;
   const int oy = (tix / f.tiles_x) * TH;
   const int ox = (tix % f.tiles_x) * TW;
   const int ny = f.ny, nx = f.nx;
+  const bool edge = (oy - 6 < 0) || (ox - 6 < 0) || (oy + TH + 6 > ny) || (ox + TW + 6 > nx);
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
-  const bool edge = (oy - HX < 0) || (ox - HX < 0) || (oy + TH + HX > ny) || (ox + TW + HX > nx);
-  bool bad = false;
 
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
-  for (int i = tid; i < Reg<6>::N; i += NT) {
-    const int ly = i / Reg<6>::W - 6, lx = i % Reg<6>::W - 6;
-    const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
-    sm.X[i] = load_x0(f, gy, gx, bad);
-    sm.Mb[i] = (uint8_t)mask_bit(Mp, f.wpr, gy, gx);
-  }
+  bool bad = false;
+  stage_x0_mask<6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
   for (int i = tid; i < TH * TW; i += NT) sm.flags[i] = 0;
-  if (tid == 0) { sm.n_sp = 0; sm.n_f = 0; sm.n_rep = 0; sm.nlist = 0; sm.nlist2 = 0; }
+  if (tid == 0) sm.nlist = 0;
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
 
-  // Step 7 of the previous iteration: I_{k-1} on R4 at flagged pixels (a
-  // compacted list; reads touch unflagged pixels only, so it is in place).
+  // Step 7 of the previous iteration: I_{k-1} = R(X0, M_{k-1}) on R4, at the
+  // flagged pixels (a compacted list; reads touch unflagged pixels only, so
+  // it is done in place).
   if (k > 1) {
     for (int b = 0; b < Reg<4>::N; b += NT) {
       const int i = b + tid;
@@ -290,57 +346,86 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
       float v;
       if (!maskmed5(sm.X, sm.Mb, Reg<6>::W, c, v)) {
         const int ly = c / Reg<6>::W - 6, lx = c % Reg<6>::W - 6;
-        v = maskmed_wide(f, Mp, oy + ly, ox + lx);
+        v = maskmed_wide(f, Mp, oy + ly, ox + lx, 3);
+        atomicAdd(&f.st->n_replace_wide, 1ull);
       }
       sm.X[c] = v;
     }
-    if (tid == 0) { sm.n_rep = n; sm.nlist = 0; }
+    if (tid == 0) { sm.nlist = 0; if (n) atomicAdd(&f.st->n_replace, (unsigned long long)n); }
     __syncthreads();
     if (edge) {
-      edge_fill<4, 6>(sm.X, oy, ox, ny, nx);
+      for (int i = tid; i < Reg<4>::N; i += NT) {
+        const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
+        const int gy = oy + ly, gx = ox + lx;
+        if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
+        sm.X[Reg<6>::idx(ly, lx)] = sm.X[Reg<6>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+      }
       __syncthreads();
     }
   }
 
-  // Steps 1-3 (L+, noise, significance) on R2, and med3(I) on R3.
-  for (int i = tid; i < Reg<2>::N; i += NT) {
-    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-    const int gy = oy + ly, gx = ox + lx;
-    if (gy < 0 || gy >= ny || gx < 0 || gx >= nx) continue;
-    const int c = Reg<6>::idx(ly, lx);
-    constexpr int P = Reg<6>::W;
-    const float v = sm.X[c], u = sm.X[c - P], d = sm.X[c + P], l = sm.X[c - 1], r = sm.X[c + 1];
-    const float vv = __fadd_rn(v, v);
-    float c1 = __fsub_rn(__fsub_rn(vv, u), l);
-    float c2 = __fsub_rn(__fsub_rn(vv, u), r);
-    float c3 = __fsub_rn(__fsub_rn(vv, d), l);
-    float c4 = __fsub_rn(__fsub_rn(vv, d), r);
-    c1 = c1 > 0.0f ? c1 : 0.0f;
-    c2 = c2 > 0.0f ? c2 : 0.0f;
-    c3 = c3 > 0.0f ? c3 : 0.0f;
-    c4 = c4 > 0.0f ? c4 : 0.0f;
-    const float L = __fmul_rn(__fadd_rn(__fadd_rn(c1, c2), __fadd_rn(c3, c4)), 0.25f);
-    const float N = noise_of(f, med5_at(sm.X, P, c));
-    sm.S[i] = __fdiv_rn(L, __fadd_rn(N, N));
-  }
-  for (int i = tid; i < Reg<3>::N; i += NT) {
-    const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
-    const int gy = oy + ly, gx = ox + lx;
-    if (gy < 0 || gy >= ny || gx < 0 || gx >= nx) continue;
-    const int c = Reg<6>::idx(ly, lx);
-    float w[9];
+  // Dense part by register blocks sharing column sorts and merges between
+  // neighbouring outputs: S on R2 (4x2 blocks of med5), med3 on the tile
+  // (8x2 blocks) written straight to its plane.  Blocks evaluate
+  // out-of-frame positions too (from clamped inputs); S there is
+  // overwritten by the edge fill, med3 there is not stored.
+  constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
+  constexpr int M_BW = 8, M_BH = 2, M_UX = TW / M_BW, M_UY = TH / M_BH;
+  constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
+  static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && TW % M_BW == 0 && TH % M_BH == 0,
+                "block tiling");
+  for (int u = tid; u < ALL_UNITS; u += NT) {
+    if (u < S_UNITS) {
+      const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
+      constexpr int P = S_BW + 4;
+      float v[(S_BH + 4) * P];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int a = 0; a < S_BH + 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) w[a * 3 + b] = sm.X[c + (a - 1) * Reg<6>::W + (b - 1)];
-    float m;
-    med3x3<float>(w, &m);
-    sm.M3[i] = m;
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)];
+      float m5[S_BH * S_BW];
+      blk_med5_4x2<float>(v, m5);
+#pragma unroll
+      for (int r = 0; r < S_BH; ++r)
+#pragma unroll
+        for (int cc = 0; cc < S_BW; ++cc) {
+          const int q = (r + 2) * P + cc + 2;
+          const float L = lplus(v[q], v[q - P], v[q + P], v[q - 1], v[q + 1]);
+          const float N = noise_of(f, m5[r * S_BW + cc]);
+          sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
+          const int ty = ly0 + r, tx = lx0 + cc;
+          if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.N[ty * TW + tx] = N;
+        }
+    } else {
+      const int m = u - S_UNITS;
+      const int ly0 = (m / M_UX) * M_BH, lx0 = (m % M_UX) * M_BW;
+      constexpr int P = M_BW + 2;
+      float v[(M_BH + 2) * P];
+#pragma unroll
+      for (int a = 0; a < M_BH + 2; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)];
+      float m3[M_BH * M_BW];
+      blk_med3_8x2<float>(v, m3);
+#pragma unroll
+      for (int r = 0; r < M_BH; ++r) {
+        const int gy = oy + ly0 + r;
+        if (gy >= ny) continue;
+        float* dst = f.m3 + (size_t)gy * nx + ox + lx0;
+#pragma unroll
+        for (int cc = 0; cc < M_BW; ++cc)
+          if (ox + lx0 + cc < nx) dst[cc] = m3[r * M_BW + cc];
+      }
+    }
   }
   __syncthreads();
   if (edge) {
-    edge_fill<2, 2>(sm.S, oy, ox, ny, nx);
-    edge_fill<3, 3>(sm.M3, oy, ox, ny, nx);
+    for (int i = tid; i < Reg<2>::N; i += NT) {
+      const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
+      const int gy = oy + ly, gx = ox + lx;
+      if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
+      sm.S[i] = sm.S[Reg<2>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+    }
     __syncthreads();
   }
 
@@ -353,58 +438,33 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     list_append(p, (uint16_t)i, sm.list, &sm.nlist);
   }
   __syncthreads();
-  {
-    const unsigned n = sm.nlist;
-    for (unsigned j = tid; j < n; j += NT) {
-      const int i = sm.list[j];
-      const int ly = i / TW, lx = i % TW;
-      const int c = Reg<2>::idx(ly, lx);
-      const float sp = __fsub_rn(sm.S[c], med5_at(sm.S, Reg<2>::W, c));
-      sm.SpL[j] = sp;
-      const int c6 = Reg<6>::idx(ly, lx);
-      const bool sat = f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel;
-      const bool sig = !sat && sp > f.sigclip;
-      sm.flags[i] = (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
+  const unsigned n = sm.nlist;
+  for (unsigned j = tid; j < n; j += NT) {
+    const int i = sm.list[j];
+    const int ly = i / TW, lx = i % TW;
+    const int c = Reg<2>::idx(ly, lx);
+    float w[25];
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[a * 5 + b] = sm.S[c + (a - 2) * Reg<2>::W + (b - 2)];
+    float m;
+    med5x5<float>(w, &m);
+    const float sp = __fsub_rn(sm.S[c], m);
+    const int gy = oy + ly, gx = ox + lx;
+    const int c6 = Reg<6>::idx(ly, lx);
+    const bool sat = f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel;
+    const bool sig = !sat && sp > f.sigclip;
+    sm.flags[i] = (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
+    if (sig) {
+      f.sp[(size_t)gy * nx + gx] = sp;
+      f.np[(size_t)gy * nx + gx] = sm.N[i];
     }
-    if (tid == 0) sm.n_sp = n;
   }
   __syncthreads();
 
-  // Steps 4-5: the fine-structure test where S' > sigclip (not saturated).
-  {
-    const unsigned n = sm.nlist;
-    for (unsigned b = 0; b < n; b += NT) {
-      const unsigned j = b + tid;
-      const bool p = j < n && (sm.flags[sm.list[j]] & 1);
-      list_append(p, (uint16_t)j, sm.list2, &sm.nlist2);
-    }
-  }
-  __syncthreads();
-  {
-    const unsigned n = sm.nlist2;
-    for (unsigned t = tid; t < n; t += NT) {
-      const int j = sm.list2[t];
-      const int i = sm.list[j];
-      const int ly = i / TW, lx = i % TW;
-      const int c3 = Reg<3>::idx(ly, lx);
-      float w[49];
-#pragma unroll
-      for (int a = 0; a < 7; ++a)
-#pragma unroll
-        for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
-      float m7;
-      med7x7<float>(w, &m7);
-      const float diff = __fsub_rn(sm.M3[c3], m7);
-      float F = diff;
-      if (f.fnorm) F = __fdiv_rn(diff, noise_of(f, med5_at(sm.X, Reg<6>::W, Reg<6>::idx(ly, lx))));
-      F = F < 0.01f ? 0.01f : F;
-      if (__fdiv_rn(sm.SpL[j], F) > f.objlim) sm.flags[i] |= 4;
-    }
-    if (tid == 0) sm.n_f = n;
-  }
-  __syncthreads();
-
-  // Bit-planes of the tile (bits beyond the frame stay 0).
+  // Bit-planes of the tile (bits beyond the frame stay 0); the candidate
+  // plane is written by fine_kernel.
   const int lane = tid & 31, warp = tid >> 5;
   for (int r = warp; r < TH * TWW; r += NT / 32) {
     const int ly = r / TWW, wd = r % TWW;
@@ -413,29 +473,21 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     const uint8_t fl = ((ox + lx) < nx && gy < ny) ? sm.flags[ly * TW + lx] : 0;
     const unsigned sig = __ballot_sync(0xffffffffu, fl & 1);
     const unsigned lo = __ballot_sync(0xffffffffu, fl & 2);
-    const unsigned cand = __ballot_sync(0xffffffffu, fl & 4);
     const int w = (ox >> 5) + wd;
     if (lane == 0 && gy < ny && w < f.wpr) {
       const size_t q = (size_t)gy * f.wpr + w;
       f.p_sig[q] = sig;
       f.p_lo[q] = lo;
-      f.p_cand[q] = cand;
     }
   }
-  if (tid == 0) {
-    if (sm.n_sp) atomicAdd(&f.st->n_sprime, (unsigned long long)sm.n_sp);
-    if (sm.n_f) atomicAdd(&f.st->n_fine, (unsigned long long)sm.n_f);
-    if (sm.n_rep) atomicAdd(&f.st->n_replace, (unsigned long long)sm.n_rep);
-  }
+  if (tid == 0 && n) atomicAdd(&f.st->n_sprime, (unsigned long long)n);
 }
 
-__device__ __forceinline__ bool iteration_runs(const FrameDesc& f, int k) {
-  if (k > f.niter) return false;
-  return k == 1 || *(volatile unsigned long long*)&f.st->fresh[k - 1] != 0;
-}
-
-__global__ void __launch_bounds__(NT) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                  unsigned total, int k, unsigned* head) {
+// MINB: resident CTAs per SM the register allocation is bounded for (the
+// variants trade registers, and so spills, against occupancy).
+template <int MINB>
+__global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                        unsigned total, int k, unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CoreSmem& sm = *reinterpret_cast<CoreSmem*>(smem_raw);
   __shared__ unsigned s_item;
@@ -452,13 +504,95 @@ __global__ void __launch_bounds__(NT) core_kernel(const FrameDesc* __restrict__ 
   }
 }
 
-// Step 6 on 32-pixel words: one thread per word of M_k.  The horizontal
-// 3-dilation of a word takes the edge bits of its neighbours.
+// ---- step 5: the fine-structure (objlim) test where S' > sigclip ----------
+
+struct FineSmem {
+  float M3[Reg<3>::N];     // med3 plane on R3 (clamped)
+  uint32_t sig[TH * TWW];  // sigclip bit-plane words of the tile
+  uint32_t cand[TH * TWW];
+  uint16_t list[TH * TW];
+  unsigned nlist;
+  int any;
+};
+
+// F = max((med3 - med7(med3)) / N, 0.01) and the objlim test S'/F > objlim
+// at the pixels whose sigclip bit is set; writes the tile's candidate words.
+__global__ void __launch_bounds__(NT) fine_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                  unsigned total, int k, unsigned* head) {
+  __shared__ FineSmem sm;
+  __shared__ unsigned s_item;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) { s_item = atomicAdd(head, 1u); sm.nlist = 0; sm.any = 0; }
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= total) break;
+    const FrameDesc& f = fr[frame_of(fr, nframes, item)];
+    if (iteration_runs(f, k)) {
+      const int tix = (int)(item - f.tile_begin);
+      const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
+      const int ny = f.ny, nx = f.nx;
+      for (int r = tid; r < TH * TWW; r += NT) {
+        const int gy = oy + r / TWW, w = (ox >> 5) + r % TWW;
+        const uint32_t v = (gy < ny && w < f.wpr) ? __ldg(f.p_sig + (size_t)gy * f.wpr + w) : 0u;
+        sm.sig[r] = v;
+        sm.cand[r] = 0u;
+        if (v) sm.any = 1;
+      }
+      __syncthreads();
+      if (sm.any) {
+#pragma unroll 4
+        for (int i = tid; i < Reg<3>::N; i += NT) {
+          const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
+          const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
+          sm.M3[i] = __ldg(f.m3 + (size_t)gy * nx + gx);
+        }
+        for (int b = 0; b < TH * TW; b += NT) {
+          const int i = b + tid;
+          const int ly = i / TW, lx = i % TW;
+          const bool p = (sm.sig[ly * TWW + (lx >> 5)] >> (lx & 31)) & 1u;
+          list_append(p, (uint16_t)i, sm.list, &sm.nlist);
+        }
+        __syncthreads();
+        const unsigned n = sm.nlist;
+        for (unsigned j = tid; j < n; j += NT) {
+          const int i = sm.list[j];
+          const int ly = i / TW, lx = i % TW;
+          const int c3 = Reg<3>::idx(ly, lx);
+          float w[49];
+#pragma unroll
+          for (int a = 0; a < 7; ++a)
+#pragma unroll
+            for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
+          float m7;
+          med7x7<float>(w, &m7);
+          const float diff = __fsub_rn(sm.M3[c3], m7);
+          const size_t q = (size_t)(oy + ly) * nx + ox + lx;
+          float F = f.fnorm ? __fdiv_rn(diff, __ldg(f.np + q)) : diff;
+          F = F < 0.01f ? 0.01f : F;
+          const float sp = __ldg(f.sp + q);
+          if (__fdiv_rn(sp, F) > f.objlim) atomicOr(&sm.cand[ly * TWW + (lx >> 5)], 1u << (lx & 31));
+        }
+        if (tid == 0 && n) atomicAdd(&f.st->n_fine, (unsigned long long)n);
+        __syncthreads();
+      }
+      for (int r = tid; r < TH * TWW; r += NT) {
+        const int gy = oy + r / TWW, w = (ox >> 5) + r % TWW;
+        if (gy < ny && w < f.wpr) f.p_cand[(size_t)gy * f.wpr + w] = sm.cand[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- step 6: growth on 32-pixel words --------------------------------------
+
 __device__ __forceinline__ uint32_t plane_word(const uint32_t* P, int ny, int wpr, int y, int w) {
   if (y < 0 || y >= ny || w < 0 || w >= wpr) return 0u;
   return __ldg(P + (size_t)y * wpr + w);
 }
 
+// Horizontal 3-dilation of word c with the edge bits of its neighbours.
 __device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
   return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
 }
@@ -475,13 +609,14 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
       const unsigned long long q = gw - f.word_begin;
       const int y = (int)(q / (unsigned)f.wpr), w = (int)(q % (unsigned)f.wpr);
       const int ny = f.ny, wpr = f.wpr;
-      // Dilated candidates on rows y-1..y+1 for words w-1..w+1.
-      uint32_t dc[3][3];
       uint32_t cand[5][5];
 #pragma unroll
       for (int a = 0; a < 5; ++a)
 #pragma unroll
         for (int b = 0; b < 5; ++b) cand[a][b] = plane_word(f.p_cand, ny, wpr, y - 2 + a, w - 2 + b);
+      // g1 = dil3(cand) & sig on rows y-1..y+1 and words w-1..w+1 (exact:
+      // the candidates of words w-2..w+2 are loaded).
+      uint32_t g1[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -489,15 +624,8 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
           uint32_t v = 0;
 #pragma unroll
           for (int a = 0; a < 3; ++a) v |= hdil(cand[r + a][b], cand[r + a][b + 1], cand[r + a][b + 2]);
-          dc[r][b] = v;
+          g1[r][b] = v & plane_word(f.p_sig, ny, wpr, y - 1 + r, w - 1 + b);
         }
-      // g1 = dil3(cand) & sig on rows y-1..y+1, words w-1..w+1; the edge words
-      // are exact where g2 of word w reads them (their inner edge bit).
-      uint32_t g1[3][3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) g1[r][b] = dc[r][b] & plane_word(f.p_sig, ny, wpr, y - 1 + r, w - 1 + b);
       uint32_t d2 = 0;
 #pragma unroll
       for (int r = 0; r < 3; ++r) d2 |= hdil(g1[r][0], g1[r][1], g1[r][2]);
@@ -509,8 +637,6 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
       cnt = __popc(g2 & ~mp);
     }
   }
-  // Per-warp reduction; lanes may belong to different frames at a frame
-  // boundary, so each lane with a count adds it (rare) unless the warp agrees.
   const int lane = threadIdx.x & 31;
   const int f0 = __shfl_sync(0xffffffffu, fi, 0);
   const bool same = __all_sync(0xffffffffu, fi == f0);
@@ -524,56 +650,70 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
   }
 }
 
-// Finalize: cleaned = I_{run} (masked median at flagged pixels), mask = M_{run}.
-__global__ void __launch_bounds__(NT) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                      unsigned total, unsigned* head) {
-  __shared__ float X[Reg<2>::N];
-  __shared__ uint8_t Mb[Reg<2>::N];
+// ---- output: cleaned frame and uint8 mask of the last mask ----------------
+
+struct FinalSmem {
+  float X[Reg<3>::N];
+  uint8_t Mb[Reg<3>::N];
+  uint32_t Mw[TH + 6][MWORDS];
+  uint16_t list[TH * TW];
+  unsigned nlist;
+};
+
+// cleaned = R(X0, M_run) (the masked median at flagged pixels, X0 elsewhere),
+// mask = M_run as uint8, the flagged count and the iterations run.  The
+// flagged pixels of a tile are compacted into a list, replaced in shared
+// memory, and the tile is then written out coalesced.
+__global__ void __launch_bounds__(NT, 4) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                         unsigned total, unsigned* head) {
+  __shared__ FinalSmem sm;
   __shared__ unsigned s_item;
-  __shared__ unsigned long long s_cnt;
   const int tid = threadIdx.x;
   for (;;) {
-    if (tid == 0) { s_item = atomicAdd(head, 1u); s_cnt = 0; }
+    if (tid == 0) { s_item = atomicAdd(head, 1u); sm.nlist = 0; }
     __syncthreads();
     const unsigned item = s_item;
-    __syncthreads();
     if (item >= total) break;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
     const int tix = (int)(item - f.tile_begin);
     const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
-    int run = f.niter;
-    for (int k = 1; k <= f.niter; ++k)
-      if (f.st->fresh[k] == 0) { run = k; break; }
+    const int run = run_of(f);
     const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
     bool bad = false;
-    for (int i = tid; i < Reg<2>::N; i += NT) {
-      const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-      const int gy = clampi(oy + ly, 0, f.ny - 1), gx = clampi(ox + lx, 0, f.nx - 1);
-      X[i] = load_x0(f, gy, gx, bad);
-      Mb[i] = (uint8_t)mask_bit(M, f.wpr, gy, gx);
-    }
+    stage_x0_mask<3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
     if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
     __syncthreads();
-    unsigned long long cnt = 0;
+    for (int b = 0; b < TH * TW; b += NT) {
+      const int i = b + tid;
+      const int ly = i / TW, lx = i % TW;
+      const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[Reg<3>::idx(ly, lx)];
+      list_append(p, (uint16_t)i, sm.list, &sm.nlist);
+    }
+    __syncthreads();
+    const unsigned n = sm.nlist;
+    // In place: reads touch unflagged pixels only, writes flagged ones.
+    for (unsigned j = tid; j < n; j += NT) {
+      const int i = sm.list[j];
+      const int ly = i / TW, lx = i % TW;
+      const int c = Reg<3>::idx(ly, lx);
+      float v;
+      if (!maskmed5(sm.X, sm.Mb, Reg<3>::W, c, v) && !maskmed7(sm.X, sm.Mb, Reg<3>::W, c, v))
+        v = maskmed_wide(f, M, oy + ly, ox + lx, 4);
+      sm.X[c] = v;
+    }
+    __syncthreads();
     for (int i = tid; i < TH * TW; i += NT) {
       const int ly = i / TW, lx = i % TW;
       const int gy = oy + ly, gx = ox + lx;
-      const bool in = gy < f.ny && gx < f.nx;
-      const int c = Reg<2>::idx(ly, lx);
-      const bool m = in && Mb[c];
-      if (in) {
-        float v = X[c];
-        if (m && !maskmed5(X, Mb, Reg<2>::W, c, v)) v = maskmed_wide(f, M, gy, gx);
+      if (gy < f.ny && gx < f.nx) {
+        const int c = Reg<3>::idx(ly, lx);
         const size_t q = (size_t)gy * f.nx + gx;
-        f.clean_out[q] = v;
-        f.mask_out[q] = m ? 1 : 0;
+        f.clean_out[q] = sm.X[c];
+        f.mask_out[q] = sm.Mb[c];
       }
-      cnt += __popc(__ballot_sync(0xffffffffu, m));
     }
-    if ((tid & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
-    __syncthreads();
     if (tid == 0) {
-      if (s_cnt) atomicAdd(&f.st->flagged, s_cnt);
+      if (n) atomicAdd(&f.st->flagged, (unsigned long long)n);
       if (tix == 0) f.st->iters_run = run;
     }
     __syncthreads();

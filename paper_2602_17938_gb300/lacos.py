@@ -38,11 +38,12 @@ class Params(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("n_levels", ctypes.c_int), ("core_ms", ctypes.c_float * MAX_NITER),
+    _fields_ = [("n_levels", ctypes.c_int),
+                ("core_ms", ctypes.c_float * MAX_NITER), ("fine_ms", ctypes.c_float * MAX_NITER),
                 ("grow_ms", ctypes.c_float * MAX_NITER),
-                ("finalize_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
+                ("final_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
                 ("n_sprime", ctypes.c_longlong), ("n_fine", ctypes.c_longlong),
-                ("n_replace", ctypes.c_longlong)]
+                ("n_replace", ctypes.c_longlong), ("n_replace_wide", ctypes.c_longlong)]
 
 
 class Result(ctypes.Structure):
@@ -182,10 +183,12 @@ class Context:
         rc = self.lib.lacos_last_profile(self.h, ctypes.byref(p))
         if rc != OK:
             raise LacosError(rc, "lacos_last_profile")
-        return {"core_ms": list(p.core_ms[:p.n_levels]), "grow_ms": list(p.grow_ms[:p.n_levels]),
-                "finalize_ms": p.finalize_ms,
+        n = p.n_levels
+        return {"core_ms": list(p.core_ms[:n]),
+                "fine_ms": list(p.fine_ms[:n]), "grow_ms": list(p.grow_ms[:n]),
+                "final_ms": p.final_ms,
                 "px_iterations": p.px_iterations, "n_sprime": p.n_sprime, "n_fine": p.n_fine,
-                "n_replace": p.n_replace}
+                "n_replace": p.n_replace, "n_replace_wide": p.n_replace_wide}
 
     def last_cuda_error(self) -> int:
         return self.lib.lacos_last_cuda_error(self.h)

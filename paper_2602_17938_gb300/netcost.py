@@ -1,11 +1,12 @@
 """Static min/max operation counts of the selection networks the kernels run.
 
-The detect kernel's "algorithmic" work, used for its ALU roofline, is the
+The core kernel's "algorithmic" work, used for its ALU roofline, is the
 number of two-input min/max operations its median networks perform per
-output pixel and iteration (dense part) plus the data-dependent sparse parts
-(S' = S - med5(S) where S exceeds the lower threshold, the fine-structure
-image where S' exceeds sigclip, and masked-median replacements), each
-counted from the generated network.  Halo recomputation is not counted.
+output pixel and iteration -- the shared-block med5 (for N) and med3
+networks, per output -- plus the data-dependent S' = S - med5(S) at the
+pixels where S exceeds the lower threshold (standalone med5 network).
+Halo recomputation is not counted.  The fine and replace kernels' work is
+counted the same way from their networks.
 """
 from __future__ import annotations
 
@@ -23,8 +24,11 @@ def counts() -> dict:
     spec.loader.exec_module(gen)
     nets = gen.build_all()
     c = {name: gen.count_ops(d, o) for name, (d, o, _, _) in nets.items()}
-    c["dense_med5_per_px"] = c["med5x5"]
-    c["fine_per_px"] = 49 * c["med3x3"] + c["med7x7"]
+    blk5 = nets["blk_med5_4x2"]
+    blk3 = nets["blk_med3_8x2"]
+    c["dense_med5_per_px"] = c["blk_med5_4x2"] / len(blk5[1])
+    c["dense_med3_per_px"] = c["blk_med3_8x2"] / len(blk3[1])
+    c["fine_per_px"] = c["med7x7"] + c["med5x5"]
     c["naive_med5_per_px"] = 25 * 24  # full sort by pairwise compare-exchange, for reference
     return c
 
@@ -32,7 +36,13 @@ def counts() -> dict:
 def detect_minmax_ops(profile: dict) -> int:
     """Min/max operations of all detect launches of one request."""
     c = counts()
-    return (profile["px_iterations"] * c["dense_med5_per_px"]
-            + profile["n_sprime"] * c["med5x5"]
-            + profile["n_fine"] * c["fine_per_px"]
-            + profile["n_replace"] * c["med5x5"])
+    return int(profile["px_iterations"] * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
+               + profile["n_sprime"] * c["med5x5"])
+
+
+def fine_minmax_ops(profile: dict) -> int:
+    return int(profile["n_fine"] * counts()["fine_per_px"])
+
+
+def replace_minmax_ops(profile: dict) -> int:
+    return int(profile["n_replace"] * counts()["med5x5"])
