@@ -44,10 +44,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2602_17938_gb300 import dist as pdist
+    return pdist.env()
 
 
 # ---------------------------------------------------------------- clocks ----
@@ -197,9 +195,9 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2602_17938_gb300 import lacos, synth, netcost
 
+    from paper_2602_17938_gb300 import dist as pdist
     spec = synth.config_specs(1)[0]
-    if rank:
-        spec.seed = (1, rank)
+    spec.seed = pdist.frame_seed(1, rank)
     frame = synth.make_frame(spec)
     ny, nx = frame.shape
     npix = ny * nx
@@ -241,12 +239,8 @@ def run_ours(args):
     barrier()
     ctx.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * npix * args.steps / 1e6 / total_s
+    total_s = pdist.max_over_ranks(sum(step_ms) / 1e3, dev)
+    value = pdist.job_throughput(npix, args.steps, ws, total_s)
 
     # Roofline of the dominant kernel (core), from the live per-launch profile.
     det_ms = [ms for p in profs for ms in p["core_ms"]]
@@ -272,12 +266,8 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         lacos.clean_host(h_frame, params, h_mask, h_clean, ctx=ctx, work=(d_frame, d_mask, d_clean))
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * npix * args.e2e_steps / 1e6 / e2e_s
+    e2e_s = pdist.max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = pdist.job_throughput(npix, args.e2e_steps, ws, e2e_s)
 
     ok_check = bool(np.array_equal(h_clean.numpy()[h_mask.numpy() == 0],
                                    frame[h_mask.numpy() == 0].astype(np.float32)))
