@@ -139,6 +139,29 @@ typedef struct {
 int lacos_set_profiling(lacos_ctx *c, int on);
 int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
 
+/* Detect-and-clean of one frame without any device allocation.  The paper
+ * has no counterpart: this serves callers that must not allocate device
+ * memory while they run -- a pipeline that plans all GPU memory at start-up
+ * and forbids cudaMalloc afterwards (an allocation can synchronise the
+ * device and break the plan), or a plugin whose host application owns the
+ * device allocator.  The scratch lives in a fixed array of
+ * LACOS_STATIC_SCRATCH_BYTES inside this library's device image, held by
+ * every GPU that loads the library until the process exits; frames whose
+ * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 5.3 Mpx,
+ * e.g. 2048 x 2048 fits, 4096 x 2048 does not -- are rejected with
+ * LACOS_ENOMEM.  Arguments, layout and results are those of lacos_submit
+ * (outputs written to the caller's d_mask and d_clean); the call queues the
+ * work on `stream`, waits for it and fills *res (may be NULL).  The first
+ * call on a device looks up the array's device address and the launch
+ * geometry for that device (no allocation); make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU -- from several host threads or streams -- race and
+ * must be serialised by the caller. */
+#define LACOS_STATIC_SCRATCH_BYTES (64u << 20)
+int lacos_run_static(const void *d_frame, lacos_dtype dt, int ny, int nx, const lacos_params *p,
+                     uint8_t *d_mask, float *d_clean, lacos_stream stream, lacos_result *res);
+
 /* Drain in-flight work, free all library memory and the context. */
 int lacos_destroy(lacos_ctx *c);
 

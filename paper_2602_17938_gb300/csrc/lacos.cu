@@ -520,3 +520,162 @@ int lacos_destroy(lacos_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point without device allocation.
+//
+// Some callers cannot allocate device memory while they run: an acquisition
+// pipeline that has planned every byte of the GPU up front and forbids
+// cudaMalloc after start-up (an allocation can synchronise the device and
+// would break its memory plan), or a host application whose own allocator
+// owns the device and lets plugins use only what they bring.  For them,
+// lacos_run_static does the whole detect-and-clean of one frame with its
+// scratch in a fixed array that is part of this library's device image:
+// every GPU that loads the library holds LACOS_STATIC_SCRATCH_BYTES for it
+// until the process exits, and no call allocates or frees anything.
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[LACOS_STATIC_SCRATCH_BYTES];
+
+struct StaticDevice {
+  bool ready = false;
+  void* scratch = nullptr;  // device address of g_static_scratch on this device
+  int num_sms = 0, bpsm_core = 1, bpsm_fine = 1, bpsm_final = 1, core_variant = 3;
+};
+std::mutex g_static_mu;
+constexpr int kStaticMaxDevices = 64;
+StaticDevice g_static_dev[kStaticMaxDevices];
+
+__global__ void store_desc_kernel(FrameDesc* dst, FrameDesc d) { *dst = d; }
+
+// Once per device, with that device current: the array's device address
+// (a host-side name of a __device__ array is not a device pointer) and the
+// launch geometry.
+cudaError_t static_setup(int dev, StaticDevice*& out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticDevice& sd = g_static_dev[dev];
+  if (!sd.ready) {
+    cudaError_t e = cudaGetSymbolAddress(&sd.scratch, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
+      const int v = std::atoi(env);
+      if (v >= 0 && v < 4) sd.core_variant = v;
+    }
+    e = cudaDeviceGetAttribute(&sd.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kCoreVariants[sd.core_variant],
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CoreSmem));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core, kCoreVariants[sd.core_variant],
+                                                        NT, sizeof(CoreSmem));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_fine, fine_kernel, NT, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, NT, 0);
+    if (e != cudaSuccess) return e;
+    sd.bpsm_core = std::max(1, sd.bpsm_core);
+    sd.bpsm_fine = std::max(1, sd.bpsm_fine);
+    sd.bpsm_final = std::max(1, sd.bpsm_final);
+    sd.ready = true;
+  }
+  out = &sd;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int nx,
+                                const lacos_params* p, uint8_t* d_mask, float* d_clean,
+                                lacos_stream stream, lacos_result* res) {
+  if (!p) return LACOS_EINVAL;
+  const FrameReq f{d_frame, (int)dt, ny, nx, *p, d_mask, d_clean};
+  if (!frame_valid(f)) return LACOS_EINVAL;
+  // The same layout as a one-frame request (heads, descriptor, state, five
+  // bit-planes, three float planes), computed without touching the heap.
+  const size_t mb = maskbuf_bytes(ny, nx);
+  const size_t off_desc = align_up(sizeof(unsigned) * kHeads);
+  const size_t off_state = off_desc + align_up(sizeof(FrameDesc));
+  const size_t off_masks = off_state + align_up(sizeof(FrameState));
+  const size_t need = off_masks + 5 * mb + 3 * plane_bytes(ny, nx);
+  if (need > (size_t)LACOS_STATIC_SCRATCH_BYTES) return LACOS_ENOMEM;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LACOS_ECUDA;
+  StaticDevice* sd = nullptr;
+  if (static_setup(dev, sd) != cudaSuccess) return LACOS_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* d = (char*)sd->scratch;
+  unsigned* heads = (unsigned*)d;
+  FrameDesc* ddesc = (FrameDesc*)(d + off_desc);
+  FrameState* dstate = (FrameState*)(d + off_state);
+  char* planes = d + off_masks;
+
+  FrameDesc h;
+  std::memset(&h, 0, sizeof(h));
+  h.x0 = f.frame;
+  h.dtype = f.dtype;
+  h.ny = ny;
+  h.nx = nx;
+  h.wpr = wpr_of(nx);
+  h.mbuf0 = (uint32_t*)planes;
+  h.mbuf1 = (uint32_t*)(planes + mb);
+  h.p_sig = (uint32_t*)(planes + 2 * mb);
+  h.p_lo = (uint32_t*)(planes + 3 * mb);
+  h.p_cand = (uint32_t*)(planes + 4 * mb);
+  h.sp = (float*)(planes + 5 * mb);
+  h.m3 = (float*)(planes + 5 * mb + plane_bytes(ny, nx));
+  h.np = (float*)(planes + 5 * mb + 2 * plane_bytes(ny, nx));
+  h.mask_out = d_mask;
+  h.clean_out = d_clean;
+  h.st = dstate;
+  h.gain = p->gain;
+  volatile float rn = p->readnoise;
+  volatile float rn2 = rn * rn;
+  h.rn2 = rn2;
+  h.satlevel = p->satlevel;
+  h.sigclip = p->sigclip;
+  volatile float lo = p->sigfrac * p->sigclip;
+  h.lo = lo;
+  h.thr_min = std::min(h.lo, h.sigclip);
+  h.objlim = p->objlim;
+  h.niter = p->niter;
+  h.fnorm = p->fine_norm;
+  h.tiles_x = (nx + TW - 1) / TW;
+  const unsigned total = (unsigned)h.tiles_x * (unsigned)((ny + TH - 1) / TH);
+  h.tile_begin = 0;
+  h.tile_end = total;
+  h.word_begin = 0;
+  const unsigned long long total_words = (unsigned long long)ny * h.wpr;
+
+  // The array keeps the previous call's contents: the descriptor is
+  // rewritten, and the queue heads, the state and M_0 are cleared.
+  store_desc_kernel<<<1, 1, 0, s>>>(ddesc, h);
+  if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;
+  if (cudaMemsetAsync(heads, 0, sizeof(unsigned) * kHeads, s) != cudaSuccess ||
+      cudaMemsetAsync(dstate, 0, sizeof(FrameState), s) != cudaSuccess ||
+      cudaMemsetAsync(h.mbuf0, 0, mb, s) != cudaSuccess)
+    return LACOS_ECUDA;
+  const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core));
+  const unsigned gfn = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_fine));
+  const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
+  const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
+  for (int k = 1; k <= p->niter; ++k) {
+    kCoreVariants[sd->core_variant]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, 1, total, k,
+                                                                       heads + kHeadCore + k);
+    fine_kernel<<<gfn, NT, 0, s>>>(ddesc, 1, total, k, heads + kHeadFine + k);
+    grow_kernel<<<gw, NT, 0, s>>>(ddesc, 1, total_words, k);
+  }
+  finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, 1, total, heads + kHeadFinal);
+  if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;
+  FrameState hs;
+  if (cudaMemcpyAsync(&hs, dstate, sizeof(FrameState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LACOS_ECUDA;
+  if (res) {
+    res->status = (hs.err & ERR_NONFINITE) ? LACOS_ENONFINITE
+                                           : ((hs.err & ERR_TIMEOUT) ? LACOS_ETIMEOUT : LACOS_OK);
+    res->iters_run = hs.iters_run;
+    res->n_flagged = (long long)hs.flagged;
+    res->latency_ms = 0.0;
+  }
+  return LACOS_OK;
+}

@@ -79,6 +79,9 @@ def load_library():
         lib.lacos_version.restype = ctypes.c_char_p
         lib.lacos_set_profiling.argtypes = [P, I]
         lib.lacos_last_profile.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.lacos_run_static.argtypes = [P, I, I, I, ctypes.POINTER(Params), P, P, P,
+                                         ctypes.POINTER(Result)]
+        lib.lacos_run_static.restype = I
         for name in ("lacos_create", "lacos_submit", "lacos_submit_batch", "lacos_poll",
                      "lacos_wait", "lacos_destroy", "lacos_last_cuda_error",
                      "lacos_set_profiling", "lacos_last_profile"):
@@ -223,6 +226,29 @@ def clean_frame(frame, gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0
     finally:
         if own:
             ctx.close()
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def run_static(frame, params: Params, mask, clean, stream=None) -> FrameResult:
+    """lacos_run_static: detect-and-clean one device frame with no device
+    allocation (scratch in the library's fixed device array; frames whose
+    scratch exceeds 64 MiB raise LacosError(ENOMEM)).  For callers that must
+    not allocate device memory while running; blocks until the frame is done.
+    Calls that overlap on the GPU share the array and must be serialised."""
+    ny, nx = frame.shape
+    for t in (frame, mask, clean):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("frame, mask and clean must be contiguous CUDA tensors")
+    r = Result()
+    rc = load_library().lacos_run_static(ctypes.c_void_p(frame.data_ptr()), _dtype_code(frame), ny, nx,
+                                         ctypes.byref(params), ctypes.c_void_p(mask.data_ptr()),
+                                         ctypes.c_void_p(clean.data_ptr()), _stream_ptr(stream),
+                                         ctypes.byref(r))
+    if rc != OK:
+        raise LacosError(rc, "lacos_run_static")
+    return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms)
 
 
 def clean_host(h_frame, params: Params, h_mask, h_clean, ctx: Context, work=None, stream=None):
