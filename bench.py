@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -179,6 +182,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ batched and served ---
+def run_batched(args, dev):
+    """64 frames of uneven sizes (2048^2 f32, 4096x3072 u16, 9576x6388 u16; the
+    config-1 recipe with per-frame gain and read noise) in one request: one
+    launch per iteration level over a shared tile queue, replayed as a CUDA graph."""
+    import torch
+    from paper_2602_17938_gb300 import lacos, synth
+    specs = synth.config_specs(2)
+    t0 = time.perf_counter()
+    frames = synth.make_frames_parallel(specs)
+    gen_s = time.perf_counter() - t0
+    d_frames = [lacos.to_device(f, dev) for f in frames]
+    del frames
+    masks = [torch.empty(f.shape, dtype=torch.uint8, device=dev) for f in d_frames]
+    cleans = [torch.empty(f.shape, dtype=torch.float32, device=dev) for f in d_frames]
+    params = [lacos.make_params(sp.gain, sp.readnoise, sp.satlevel, sp.sigclip, sp.sigfrac,
+                                sp.objlim, sp.niter) for sp in specs]
+    npix = sum(sp.npix for sp in specs)
+    ctx = lacos.Context(dev.index or 0, hbm_budget_bytes=96 << 30, max_slots=2)
+    stream = torch.cuda.current_stream(dev)
+    t, _ = ctx.submit_batch(d_frames, params, masks, cleans, reuse_graph=True)  # capture
+    ctx.wait(t)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.batched_steps)]
+    flagged = 0
+    for a, b in ev:
+        a.record(stream)
+        t, per = ctx.submit_batch(d_frames, params, masks, cleans, reuse_graph=True)
+        b.record(stream)
+        r = ctx.wait(t)
+        flagged = r.n_flagged
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ctx.close()
+    del d_frames, masks, cleans
+    torch.cuda.empty_cache()
+    return {"workload": "64 frames: 16x 2048x2048 f32, 16x 4096x3072 u16, 32x 9576x6388 u16 "
+                        "(seed 2), niter=4, one request, CUDA-graph replay",
+            "mpix_per_s": npix / 1e6 / (sum(ms) / 1e3 / len(ms)), "ms_per_batch": sum(ms) / len(ms),
+            "mpix_per_batch": npix / 1e6, "steps": len(ms), "n_flagged": flagged,
+            "frame_generation_s": gen_s, "l2": "inputs (4.6 GB) far exceed L2"}
+
+
+def run_serving(args, dev):
+    """Poisson stream of 9576x6388 u16 frames with 10% 2048x2048 f32 frames,
+    admitted by a 120 GB HBM budget, requests overlapping on the device."""
+    import math
+    import torch
+    from paper_2602_17938_gb300 import lacos, serve, synth
+    specs = synth.config_specs(3, count=200)
+    big = [sp for sp in specs if sp.ny == 6388][:4]
+    small = [sp for sp in specs if sp.ny == 2048][:2]
+    pool_specs = big + small
+    pool = [lacos.to_device(f, dev) for f in synth.make_frames_parallel(pool_specs)]
+    p = lacos.make_params(1.0, 1.5)
+    kinds = [0 if sp.ny == 6388 else 1 for sp in specs]
+    points = []
+    with serve.Server(dev.index or 0, hbm_budget_bytes=120 << 30, max_slots=96) as srv:
+        for rate, n in ((1.1, 12), (8.0, 48), (32.0, 120), (math.inf, 160)):
+            arr = synth.poisson_arrivals(rate, n) if math.isfinite(rate) else [0.0] * n
+            reqs = []
+            for i in range(n):
+                fr = pool[i % 4] if kinds[i % len(kinds)] == 0 else pool[4 + i % 2]
+                reqs.append(serve.Request(fr, p, float(arr[i] - arr[0])))
+            st = srv.run(reqs)
+            points.append({"rate_hz": rate if math.isfinite(rate) else "saturation", "requests": n,
+                           "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                           "mpix_per_s": st.mpix_per_s, "max_in_flight": st.max_in_flight})
+    del pool
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson arrivals of 9576x6388 u16 frames, 10% 2048x2048 f32 (seed 3); "
+                        "6 distinct frames reused round-robin; 120 GB HBM budget; lacos_submit_async",
+            "points": points}
+
+
 # ------------------------------------------------------------- GPU arm -----
 def alu_peak():
     import ctypes
@@ -221,6 +300,8 @@ def run_ours(args):
                                spec.sigfrac, spec.objlim, spec.niter)
     ctx = lacos.Context(local)
     stream = torch.cuda.current_stream(dev)
+    from paper_2602_17938_gb300 import autotune
+    variant, variant_ms = autotune.tune(ctx, d_frame, params, d_mask, d_clean)
 
     def barrier():
         if ws > 1:
@@ -284,6 +365,13 @@ def run_ours(args):
     ok_check = bool(np.array_equal(h_clean.numpy()[h_mask.numpy() == 0],
                                    frame[h_mask.numpy() == 0].astype(np.float32)))
     ctx.close()
+    del d_frame, d_mask, d_clean, flush
+    torch.cuda.empty_cache()
+    batched = serving = None
+    if ws == 1 and not args.no_batched:
+        batched = run_batched(args, dev)
+    if ws == 1 and not args.no_serving:
+        serving = run_serving(args, dev)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else oracle_sample(frame, spec)
@@ -311,6 +399,14 @@ def run_ours(args):
         "alu_peak_gops": {"f32": peak_f32, "u16x2": peak_u16},
         "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_fine", "n_replace", "n_replace_wide")},
     }
+    line["core_variant"] = {"chosen": variant, "ms_per_variant": variant_ms}
+    if batched:
+        line["batched"] = batched
+    if serving:
+        line["serving"] = serving
+        sat = serving["points"][0]
+        line["p99_latency_ms"] = sat["p99_ms"]
+        line["p99_latency_at"] = f"{sat['rate_hz']} frames/s Poisson, 120 GB budget"
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -98,6 +98,16 @@ int lacos_submit(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int 
                  const lacos_params *p, uint8_t *d_mask, float *d_clean,
                  lacos_stream stream, unsigned long long *ticket);
 
+/* As lacos_submit, but the request runs on a stream of its own (one per
+ * slot, created on first use), so requests submitted back to back overlap
+ * on the device -- the continuous batching of the serving loop: a request is
+ * admitted as soon as a slot and budget are free, whatever is still running.
+ * The work is ordered after nothing the caller queued: the frame must
+ * already be complete on the device when the call is made. */
+int lacos_submit_async(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int nx,
+                       const lacos_params *p, uint8_t *d_mask, float *d_clean,
+                       unsigned long long *ticket);
+
 /* Non-blocking completion check.  Returns LACOS_PENDING while the request
  * runs; otherwise fills *res, releases the request's slot and returns
  * LACOS_OK (res->status carries LACOS_ENONFINITE/LACOS_ETIMEOUT if the device
@@ -161,6 +171,18 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
 #define LACOS_STATIC_SCRATCH_BYTES (64u << 20)
 int lacos_run_static(const void *d_frame, lacos_dtype dt, int ny, int nx, const lacos_params *p,
                      uint8_t *d_mask, float *d_clean, lacos_stream stream, lacos_result *res);
+
+/* Core-kernel variant of the context (0..3: register allocation bounded for
+ * 1..4 resident CTAs per SM; more CTAs hide more latency, fewer registers
+ * spill more).  lacos_autotune runs the given frame `reps` times (after one
+ * warm-up) with each variant, keeps the fastest, and reports each variant's
+ * mean device time in variant_ms[4] (may be NULL).  Results do not depend
+ * on the variant. */
+int lacos_set_core_variant(lacos_ctx *c, int variant);
+int lacos_get_core_variant(lacos_ctx *c, int *variant);
+int lacos_autotune(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int nx,
+                   const lacos_params *p, uint8_t *d_mask, float *d_clean, lacos_stream stream,
+                   int reps, int *best_variant, float *variant_ms);
 
 /* Drain in-flight work, free all library memory and the context. */
 int lacos_destroy(lacos_ctx *c);

@@ -59,6 +59,7 @@ struct Slot {
   cudaGraphExec_t gexec = nullptr;
   std::vector<FrameReq> graph_key;
   cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be uncapturable)
+  cudaStream_t own_stream = nullptr;  // the slot's own stream (lacos_submit_async)
   // Profiling events (see enqueue).
   std::vector<cudaEvent_t> prof_ev;
   int prof_n = -1;  // levels recorded for the request in flight (-1: none)
@@ -270,7 +271,8 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
 }
 
 static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream_t s,
-                       int reuse_graph, lacos_result* per_frame, unsigned long long* ticket) {
+                       int reuse_graph, lacos_result* per_frame, unsigned long long* ticket,
+                       bool own_stream = false) {
   if (!c || !ticket || fr.empty()) return LACOS_EINVAL;
   for (const auto& f : fr)
     if (!frame_valid(f)) return LACOS_EINVAL;
@@ -287,6 +289,10 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream
     for (auto& x : c->slots)
       if (!x.busy) { sl = &x; break; }
   if (!sl) return LACOS_EAGAIN;
+  if (own_stream) {
+    if (!sl->own_stream) CK(cudaStreamCreateWithFlags(&sl->own_stream, cudaStreamNonBlocking));
+    s = sl->own_stream;
+  }
   if (sl->dcap < L.total) {
     if (sl->dscratch) {
       CK(cudaFreeAsync(sl->dscratch, s));
@@ -455,6 +461,55 @@ int lacos_submit_batch(lacos_ctx* c, int n, const void* const* d_frames, const i
   return submit_impl(c, fr, (cudaStream_t)stream, reuse_graph, per_frame, ticket);
 }
 
+int lacos_submit_async(lacos_ctx* c, const void* d_frame, lacos_dtype dt, int ny, int nx,
+                       const lacos_params* p, uint8_t* d_mask, float* d_clean,
+                       unsigned long long* ticket) {
+  if (!p) return LACOS_EINVAL;
+  std::vector<FrameReq> fr{{d_frame, (int)dt, ny, nx, *p, d_mask, d_clean}};
+  return submit_impl(c, fr, nullptr, 0, nullptr, ticket, true);
+}
+
+int lacos_set_core_variant(lacos_ctx* c, int variant) {
+  if (!c || variant < 0 || variant > 3) return LACOS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->core_variant = variant;
+  return LACOS_OK;
+}
+
+int lacos_get_core_variant(lacos_ctx* c, int* variant) {
+  if (!c || !variant) return LACOS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *variant = c->core_variant;
+  return LACOS_OK;
+}
+
+int lacos_autotune(lacos_ctx* c, const void* d_frame, lacos_dtype dt, int ny, int nx,
+                   const lacos_params* p, uint8_t* d_mask, float* d_clean, lacos_stream stream,
+                   int reps, int* best_variant, float* variant_ms) {
+  if (!c || !p || reps < 1) return LACOS_EINVAL;
+  int best = -1;
+  float best_ms = 0.0f;
+  for (int v = 0; v < 4; ++v) {
+    int rc = lacos_set_core_variant(c, v);
+    if (rc) return rc;
+    double sum = 0.0;
+    for (int r = 0; r <= reps; ++r) {  // the first run warms up
+      unsigned long long t = 0;
+      lacos_result res{};
+      rc = lacos_submit(c, d_frame, dt, ny, nx, p, d_mask, d_clean, stream, &t);
+      if (rc) return rc;
+      rc = lacos_wait(c, t, &res);
+      if (rc) return rc;
+      if (r > 0) sum += res.latency_ms;
+    }
+    const float ms = (float)(sum / reps);
+    if (variant_ms) variant_ms[v] = ms;
+    if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+  }
+  if (best_variant) *best_variant = best;
+  return lacos_set_core_variant(c, best);
+}
+
 int lacos_poll(lacos_ctx* c, unsigned long long ticket, lacos_result* res) {
   if (!c) return LACOS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -514,6 +569,7 @@ int lacos_destroy(lacos_ctx* c) {
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
     for (cudaEvent_t e : sl.prof_ev) cudaEventDestroy(e);
     if (sl.cap_stream) cudaStreamDestroy(sl.cap_stream);
+    if (sl.own_stream) cudaStreamDestroy(sl.own_stream);
   }
   delete c;
   return rc;

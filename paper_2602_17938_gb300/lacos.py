@@ -82,6 +82,14 @@ def load_library():
         lib.lacos_run_static.argtypes = [P, I, I, I, ctypes.POINTER(Params), P, P, P,
                                          ctypes.POINTER(Result)]
         lib.lacos_run_static.restype = I
+        lib.lacos_submit_async.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P, U64P]
+        lib.lacos_set_core_variant.argtypes = [P, I]
+        lib.lacos_get_core_variant.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+        lib.lacos_autotune.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P, P, I,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        for name in ("lacos_submit_async", "lacos_set_core_variant", "lacos_get_core_variant",
+                     "lacos_autotune"):
+            getattr(lib, name).restype = I
         for name in ("lacos_create", "lacos_submit", "lacos_submit_batch", "lacos_poll",
                      "lacos_wait", "lacos_destroy", "lacos_last_cuda_error",
                      "lacos_set_profiling", "lacos_last_profile"):
@@ -140,6 +148,45 @@ class Context:
         if rc != OK:
             raise LacosError(rc, "lacos_submit")
         return t.value
+
+    def submit_async(self, frame, params: Params, mask, clean) -> int:
+        """Queue one frame on a stream of its own (requests overlap on the device).
+        The frame must already be complete on the device.  Raises LacosError(EAGAIN)
+        when no slot or budget is free."""
+        ny, nx = frame.shape
+        t = ctypes.c_ulonglong(0)
+        rc = self.lib.lacos_submit_async(self.h, ctypes.c_void_p(frame.data_ptr()), _dtype_code(frame),
+                                         ny, nx, ctypes.byref(params), ctypes.c_void_p(mask.data_ptr()),
+                                         ctypes.c_void_p(clean.data_ptr()), ctypes.byref(t))
+        if rc != OK:
+            raise LacosError(rc, "lacos_submit_async")
+        return t.value
+
+    def set_core_variant(self, v: int):
+        rc = self.lib.lacos_set_core_variant(self.h, int(v))
+        if rc != OK:
+            raise LacosError(rc, "lacos_set_core_variant")
+
+    def core_variant(self) -> int:
+        v = ctypes.c_int(0)
+        rc = self.lib.lacos_get_core_variant(self.h, ctypes.byref(v))
+        if rc != OK:
+            raise LacosError(rc, "lacos_get_core_variant")
+        return v.value
+
+    def autotune(self, frame, params: Params, mask, clean, reps: int = 2, stream=None):
+        """Time every core-kernel variant on this frame and keep the fastest.
+        Returns (best variant, [mean ms per variant])."""
+        ny, nx = frame.shape
+        best = ctypes.c_int(-1)
+        ms = (ctypes.c_float * 4)()
+        rc = self.lib.lacos_autotune(self.h, ctypes.c_void_p(frame.data_ptr()), _dtype_code(frame), ny, nx,
+                                     ctypes.byref(params), ctypes.c_void_p(mask.data_ptr()),
+                                     ctypes.c_void_p(clean.data_ptr()), _stream_ptr(stream), int(reps),
+                                     ctypes.byref(best), ms)
+        if rc != OK:
+            raise LacosError(rc, "lacos_autotune")
+        return best.value, list(ms)
 
     def submit_batch(self, frames, params, masks, cleans, stream=None, reuse_graph=False):
         """Queue a batch of frames (any sizes/dtypes); returns (ticket, per-frame result array)."""

@@ -199,3 +199,15 @@ def poisson_arrivals(rate_hz: float, n: int, seed=(3, 1 << 21)) -> np.ndarray:
     """Arrival times (s) of a Poisson stream with ``rate_hz`` requests per second."""
     rng = _rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_hz, n))
+
+
+def make_frames_parallel(specs: list[FrameSpec], workers: int | None = None) -> list[np.ndarray]:
+    """make_frame over many specs on a thread pool (the same frames, faster:
+    numpy's heavy parts release the GIL; no child processes are involved)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    n = workers or min(len(specs), os.cpu_count() or 1)
+    if n <= 1 or len(specs) <= 1:
+        return [make_frame(s) for s in specs]
+    with ThreadPoolExecutor(n) as ex:
+        return list(ex.map(make_frame, specs))

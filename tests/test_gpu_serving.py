@@ -1,0 +1,129 @@
+"""Serving (continuous admission, overlapping requests) and the core-variant autotuner.
+
+Every request's mask and cleaned frame must be identical -- bit for bit,
+the tolerance of every GPU test here -- whether it runs alone or in a mix
+of overlapping requests of other sizes, dtypes and parameters, and
+whichever core-kernel variant runs it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_17938_gb300 import build, lacos
+    build.build()
+    return lacos
+
+
+def _frame(ny, nx, seed, dtype=np.float32, sky=100.0):
+    rng = np.random.default_rng(seed)
+    f = sky + math.sqrt(sky + 2.25) * rng.standard_normal((ny, nx))
+    n = max(1, ny * nx // 100)
+    f[rng.integers(0, ny, n), rng.integers(0, nx, n)] += rng.uniform(200, 4000, n)
+    if dtype == np.uint16:
+        return np.clip(np.rint(f), 0, 65535).astype(np.uint16)
+    return f.astype(np.float32)
+
+
+def _mix(lacos):
+    shapes = [(300, 410, np.float32), (517, 260, np.uint16), (96, 1000, np.float32),
+              (640, 640, np.uint16), (33, 77, np.float32), (450, 455, np.uint16)]
+    frames = [_frame(ny, nx, 40 + i, dt) for i, (ny, nx, dt) in enumerate(shapes)]
+    params = [lacos.make_params(0.6 + 0.2 * i, 1.0 + 0.3 * i, niter=(1, 4, 6)[i % 3],
+                                sigclip=(4.5, 4.0, 5.0)[i % 3]) for i in range(len(frames))]
+    return frames, params
+
+
+def test_each_result_same_alone_and_in_the_mix(lib):
+    from paper_2602_17938_gb300 import serve
+    lacos = lib
+    frames, params = _mix(lacos)
+    dev = [lacos.to_device(f) for f in frames]
+    alone = []
+    with lacos.Context(0) as ctx:
+        for d, p in zip(dev, params):
+            m = torch.empty(d.shape, dtype=torch.uint8, device="cuda")
+            c = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+            r = ctx.wait(ctx.submit(d, p, m, c))
+            alone.append((m.cpu(), c.cpu(), r))
+    # 3 rounds of the 6 frames, all arriving at once: up to 18 requests overlap.
+    reqs = [serve.Request(dev[i % 6], params[i % 6], 0.0) for i in range(18)]
+    with serve.Server(0, hbm_budget_bytes=4 << 30, max_slots=18, keep_outputs=True) as srv:
+        st = srv.run(reqs)
+        torch.cuda.synchronize()
+        assert st.n == 18 and st.max_in_flight > 1
+        for rec in st.records:
+            m, c, r = alone[rec.index % 6]
+            assert rec.result.status == 0
+            assert rec.result.n_flagged == r.n_flagged and rec.result.iters_run == r.iters_run
+            assert torch.equal(rec.mask.cpu(), m)
+            assert torch.equal(rec.clean.cpu().view(torch.int32), c.view(torch.int32))
+    # and the alone results are the oracle's
+    for f, p, (m, c, r) in zip(frames, params, alone):
+        mr, cr, it, nf = oracle.run(f, p.gain, p.readnoise, p.satlevel, p.sigclip, p.sigfrac,
+                                    p.objlim, p.niter)
+        assert np.array_equal(m.numpy(), mr) and np.array_equal(c.numpy().view(np.uint32), cr.view(np.uint32))
+
+
+def test_budget_limits_requests_in_flight(lib):
+    from paper_2602_17938_gb300 import serve
+    lacos = lib
+    f = lacos.to_device(_frame(512, 512, 5))
+    p = lacos.make_params(1.0, 1.5)
+    with serve.Server(0, hbm_budget_bytes=1, max_slots=8) as srv:
+        one = srv._request_bytes(512, 512)
+    # room for one request at a time (plus the context's scratch for it)
+    with serve.Server(0, hbm_budget_bytes=int(1.5 * one), max_slots=8) as srv:
+        st = srv.run([serve.Request(f, p, 0.0) for _ in range(5)])
+        assert st.n == 5 and st.max_in_flight == 1
+    with serve.Server(0, hbm_budget_bytes=int(3.5 * one), max_slots=8) as srv:
+        st = srv.run([serve.Request(f, p, 0.0) for _ in range(6)])
+        assert st.n == 6 and 1 < st.max_in_flight <= 3
+
+
+def test_poisson_stream_completes(lib):
+    from paper_2602_17938_gb300 import serve
+    lacos = lib
+    frames, params = _mix(lacos)
+    dev = [lacos.to_device(f) for f in frames]
+    reqs = serve.poisson_requests(dev, params, rate_hz=400.0, n=24)
+    with serve.Server(0, hbm_budget_bytes=4 << 30, max_slots=16) as srv:
+        st = srv.run(reqs)
+    assert st.n == 24 and all(r.result.status == 0 for r in st.records)
+    assert 0 < st.p50_ms <= st.p99_ms and st.mpix_per_s > 0
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint16])
+def test_every_core_variant_bit_exact_and_autotune(lib, dtype, tmp_path, monkeypatch):
+    lacos = lib
+    f = _frame(333, 517, 9, dtype)
+    d = lacos.to_device(f)
+    p = lacos.make_params(1.0, 1.5, niter=4)
+    mr, cr, it, nf = oracle.run(f, 1.0, 1.5)
+    m = torch.empty(f.shape, dtype=torch.uint8, device="cuda")
+    c = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+    with lacos.Context(0) as ctx:
+        for v in range(4):
+            ctx.set_core_variant(v)
+            assert ctx.core_variant() == v
+            r = ctx.wait(ctx.submit(d, p, m, c))
+            assert r.iters_run == it and r.n_flagged == nf
+            assert np.array_equal(m.cpu().numpy(), mr)
+            assert np.array_equal(c.cpu().numpy().view(np.uint32), cr.view(np.uint32))
+        monkeypatch.setenv("LACOS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+        from paper_2602_17938_gb300 import autotune
+        best, ms = autotune.tune(ctx, d, p, m, c, reps=1)
+        assert 0 <= best <= 3 and ctx.core_variant() == best and len(ms) == 4
+        best2, ms2 = autotune.tune(ctx, d, p, m, c)  # from the cache
+        assert best2 == best and ms2 is None
