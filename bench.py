@@ -338,7 +338,7 @@ def run_ours(args):
     # Roofline of the dominant kernel (core), from the live per-launch profile.
     det_ms = [ms for p in profs for ms in p["core_ms"]]
     per_kernel = {name: sum(ms for p in profs for ms in p[name + "_ms"])
-                  for name in ("core", "fine", "grow")}
+                  for name in ("core", "grow")}
     per_kernel["final"] = sum(p["final_ms"] for p in profs)
     n_launch = len(det_ms)
     ops = sum(netcost.detect_minmax_ops(p) for p in profs)
@@ -392,7 +392,7 @@ def run_ours(args):
                      "kernel_ms_per_step": {k: v / len(profs) for k, v in per_kernel.items()}},
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": 2 * npix,
                 "d2h_bytes_per_step": 5 * npix},
-        "gpu_launches": args.steps * (3 * spec.niter + 1),
+        "gpu_launches": args.steps * (2 * spec.niter + 1),
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
         "check_clean_equals_input_outside_mask": ok_check,

@@ -26,7 +26,7 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (12.6 bytes per pixel plus a few kilobytes per request),
+ * its scratch (5 bits per pixel plus a few kilobytes per request),
  * charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
@@ -135,8 +135,7 @@ int lacos_submit_batch(lacos_ctx *c, int n, const void *const *d_frames, const i
  * its stream, so requests replayed from a CUDA graph are not profiled). */
 typedef struct {
   int n_levels;                        /* iteration levels launched */
-  float core_ms[LACOS_MAX_NITER];      /* per level: step 7 of the previous level, steps 1-4 */
-  float fine_ms[LACOS_MAX_NITER];      /* per level: step 5 (fine structure, objlim) */
+  float core_ms[LACOS_MAX_NITER];      /* per level: step 7 of the previous level, steps 1-5 */
   float grow_ms[LACOS_MAX_NITER];      /* per level: step 6 (growth, mask update) */
   float final_ms;                      /* cleaned frame (last step 7) and uint8 mask */
   long long px_iterations;             /* sum over frames of ny*nx*iters_run */
@@ -157,8 +156,8 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
  * device allocator.  The scratch lives in a fixed array of
  * LACOS_STATIC_SCRATCH_BYTES inside this library's device image, held by
  * every GPU that loads the library until the process exits; frames whose
- * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 5.3 Mpx,
- * e.g. 2048 x 2048 fits, 4096 x 2048 does not -- are rejected with
+ * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 107 Mpx,
+ * e.g. 9576 x 6388 fits, 12000 x 12000 does not -- are rejected with
  * LACOS_ENOMEM.  Arguments, layout and results are those of lacos_submit
  * (outputs written to the caller's d_mask and d_clean); the call queues the
  * work on `stream`, waits for it and fills *res (may be NULL).  The first

@@ -7,7 +7,7 @@
 // against the context's HBM budget.  The request's work is queued on the
 // caller's stream:
 //   memcpy(descriptors) ; memset(state, heads, M_0) ;
-//   { core_kernel(k) ; fine_kernel(k) ; grow_kernel(k) } for k = 1..max niter ;
+//   { core_kernel(k) ; grow_kernel(k) } for k = 1..max niter ;
 //   finalize_kernel ;
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
@@ -33,8 +33,8 @@ namespace {
 constexpr size_t kAlign = 256;
 // Tile-queue heads: one per (kernel, level) plus the final replace.
 constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
-constexpr int kHeadCore = 0, kHeadFine = kHeadLevels;
-constexpr int kHeadFinal = 2 * kHeadLevels, kHeads = 2 * kHeadLevels + 1;
+constexpr int kHeadCore = 0;
+constexpr int kHeadFinal = kHeadLevels, kHeads = kHeadLevels + 1;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 struct FrameReq {
@@ -79,7 +79,6 @@ bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) 
 
 int wpr_of(int nx) { return (nx + 31) / 32; }
 size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
-size_t plane_bytes(int ny, int nx) { return align_up((size_t)ny * nx * sizeof(float)); }
 
 struct Layout {
   size_t heads, descs, states, masks, total;
@@ -96,7 +95,7 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 5 * maskbuf_bytes(f.ny, f.nx) + 3 * plane_bytes(f.ny, f.nx);  // M 0/1, sig/lo/cand, S', med3, N
+    off += 5 * maskbuf_bytes(f.ny, f.nx);  // M buffers 0/1, planes sig/lo/cand
   }
   L.total = off;
   return L;
@@ -116,7 +115,6 @@ struct lacos_ctx {
   int core_variant = 3;                 // index into kCoreVariants
   int blocks_per_sm_core_v[4] = {1, 1, 1, 1};
   int blocks_per_sm_core = 1;
-  int blocks_per_sm_fine = 1;
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
@@ -197,9 +195,6 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_sig = (uint32_t*)(d + L.mask_off[i] + 2 * mb);
     h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
-    h.sp = (float*)(d + L.mask_off[i] + 5 * mb);
-    h.m3 = (float*)(d + L.mask_off[i] + 5 * mb + plane_bytes(f.ny, f.nx));
-    h.np = (float*)(d + L.mask_off[i] + 5 * mb + 2 * plane_bytes(f.ny, f.nx));
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -232,12 +227,11 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   const int nf = (int)fr.size();
   const int cv = c->core_variant;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core_v[cv]));
-  const unsigned gfn = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_fine));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
   const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
-  // Profile events: [0] start, level k: [3k-2] after core, [3k-1] after
-  // fine, [3k] after grow, [3n+1] after finalize.
-  const int nev = 3 * max_niter + 2;
+  // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
+  // [2n+1] after finalize.
+  const int nev = 2 * max_niter + 2;
   if (prof) {
     while ((int)sl.prof_ev.size() < nev) {
       cudaEvent_t e;
@@ -253,17 +247,14 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   for (int k = 1; k <= max_niter; ++k) {
     kCoreVariants[cv]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
     CK(cudaGetLastError());
-    if (int rc = mark(3 * k - 2)) return rc;
-    fine_kernel<<<gfn, NT, 0, s>>>(ddesc, nf, total, k, heads + kHeadFine + k);
-    CK(cudaGetLastError());
-    if (int rc = mark(3 * k - 1)) return rc;
+    if (int rc = mark(2 * k - 1)) return rc;
     grow_kernel<<<gw, NT, 0, s>>>(ddesc, nf, total_words, k);
     CK(cudaGetLastError());
-    if (int rc = mark(3 * k)) return rc;
+    if (int rc = mark(2 * k)) return rc;
   }
   finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, nf, total, heads + kHeadFinal);
   CK(cudaGetLastError());
-  if (int rc = mark(3 * max_niter + 1)) return rc;
+  if (int rc = mark(2 * max_niter + 1)) return rc;
   sl.prof_n = prof ? max_niter : -1;
   FrameState* hstate = (FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * fr.size()));
   CK(cudaMemcpyAsync(hstate, dstate, sizeof(FrameState) * fr.size(), cudaMemcpyDeviceToHost, s));
@@ -366,11 +357,10 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
     P.n_levels = sl.prof_n;
     const auto& E = sl.prof_ev;
     for (int k = 1; k <= sl.prof_n; ++k) {
-      cudaEventElapsedTime(&P.core_ms[k - 1], E[3 * k - 3], E[3 * k - 2]);
-      cudaEventElapsedTime(&P.fine_ms[k - 1], E[3 * k - 2], E[3 * k - 1]);
-      cudaEventElapsedTime(&P.grow_ms[k - 1], E[3 * k - 1], E[3 * k]);
+      cudaEventElapsedTime(&P.core_ms[k - 1], E[2 * k - 2], E[2 * k - 1]);
+      cudaEventElapsedTime(&P.grow_ms[k - 1], E[2 * k - 1], E[2 * k]);
     }
-    cudaEventElapsedTime(&P.final_ms, E[3 * sl.prof_n], E[3 * sl.prof_n + 1]);
+    cudaEventElapsedTime(&P.final_ms, E[2 * sl.prof_n], E[2 * sl.prof_n + 1]);
     for (int i = 0; i < sl.nframes; ++i) {
       P.px_iterations += sl.npix[i] * hs[i].iters_run;
       P.n_sprime += (long long)hs[i].n_sprime;
@@ -429,14 +419,11 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   }
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, NT, 0);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_fine, fine_kernel, NT, 0);
   if (e != cudaSuccess) {
     delete c;
     return LACOS_ECUDA;
   }
   c->blocks_per_sm_final = std::max(1, c->blocks_per_sm_final);
-  c->blocks_per_sm_fine = std::max(1, c->blocks_per_sm_fine);
   *out = c;
   return LACOS_OK;
 }
@@ -596,7 +583,7 @@ __device__ __align__(256) unsigned char g_static_scratch[LACOS_STATIC_SCRATCH_BY
 struct StaticDevice {
   bool ready = false;
   void* scratch = nullptr;  // device address of g_static_scratch on this device
-  int num_sms = 0, bpsm_core = 1, bpsm_fine = 1, bpsm_final = 1, core_variant = 3;
+  int num_sms = 0, bpsm_core = 1, bpsm_final = 1, core_variant = 3;
 };
 std::mutex g_static_mu;
 constexpr int kStaticMaxDevices = 64;
@@ -625,12 +612,9 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core, kCoreVariants[sd.core_variant],
                                                         NT, sizeof(CoreSmem));
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_fine, fine_kernel, NT, 0);
-    if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, NT, 0);
     if (e != cudaSuccess) return e;
     sd.bpsm_core = std::max(1, sd.bpsm_core);
-    sd.bpsm_fine = std::max(1, sd.bpsm_fine);
     sd.bpsm_final = std::max(1, sd.bpsm_final);
     sd.ready = true;
   }
@@ -647,12 +631,12 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const FrameReq f{d_frame, (int)dt, ny, nx, *p, d_mask, d_clean};
   if (!frame_valid(f)) return LACOS_EINVAL;
   // The same layout as a one-frame request (heads, descriptor, state, five
-  // bit-planes, three float planes), computed without touching the heap.
+  // bit-planes), computed without touching the heap.
   const size_t mb = maskbuf_bytes(ny, nx);
   const size_t off_desc = align_up(sizeof(unsigned) * kHeads);
   const size_t off_state = off_desc + align_up(sizeof(FrameDesc));
   const size_t off_masks = off_state + align_up(sizeof(FrameState));
-  const size_t need = off_masks + 5 * mb + 3 * plane_bytes(ny, nx);
+  const size_t need = off_masks + 5 * mb;
   if (need > (size_t)LACOS_STATIC_SCRATCH_BYTES) return LACOS_ENOMEM;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LACOS_ECUDA;
@@ -677,9 +661,6 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.p_sig = (uint32_t*)(planes + 2 * mb);
   h.p_lo = (uint32_t*)(planes + 3 * mb);
   h.p_cand = (uint32_t*)(planes + 4 * mb);
-  h.sp = (float*)(planes + 5 * mb);
-  h.m3 = (float*)(planes + 5 * mb + plane_bytes(ny, nx));
-  h.np = (float*)(planes + 5 * mb + 2 * plane_bytes(ny, nx));
   h.mask_out = d_mask;
   h.clean_out = d_clean;
   h.st = dstate;
@@ -711,13 +692,11 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
       cudaMemsetAsync(h.mbuf0, 0, mb, s) != cudaSuccess)
     return LACOS_ECUDA;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core));
-  const unsigned gfn = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_fine));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
   const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
   for (int k = 1; k <= p->niter; ++k) {
     kCoreVariants[sd->core_variant]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, 1, total, k,
                                                                        heads + kHeadCore + k);
-    fine_kernel<<<gfn, NT, 0, s>>>(ddesc, 1, total, k, heads + kHeadFine + k);
     grow_kernel<<<gw, NT, 0, s>>>(ddesc, 1, total_words, k);
   }
   finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, 1, total, heads + kHeadFinal);

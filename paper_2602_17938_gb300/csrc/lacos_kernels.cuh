@@ -72,9 +72,6 @@ struct FrameDesc {
   uint32_t* p_sig;   // bit-planes of the current iteration (ny x wpr words each)
   uint32_t* p_lo;
   uint32_t* p_cand;
-  float* sp;         // S' plane (written where S' > sigclip)
-  float* m3;         // med3(I) plane
-  float* np;         // N plane (written where S' > sigclip)
   uint8_t* mask_out;
   float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
@@ -260,10 +257,16 @@ struct CoreSmem {
   uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
   float S[Reg<2>::N];        // S on R2
   float N[TH * TW];          // N on the tile
+  float M3[Reg<3>::N];       // med3(I) on R3
   uint16_t list[Reg<4>::N];  // work lists (replacement on R4, then S' on the tile)
-  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo (both not saturated)
-  unsigned nlist;
+  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo (both not saturated),
+                             // bit2: candidate, bit3: saturated
+  unsigned nlist, nlist2;
 };
+// Once the dense part is done the working image is dead; its storage then
+// holds S' of the S' list entries and the fine-structure work list.
+static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * Reg<6>::N,
+              "S' and the second list must fit in the working-image storage");
 
 // Stages X0 and the mask M (clamped coordinates) on region H of a tile:
 // X (Reg<H>-indexed floats), Mb (bytes), via the mask words of the rows.
@@ -318,7 +321,6 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
   bool bad = false;
   stage_x0_mask<6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
-  for (int i = tid; i < TH * TW; i += NT) sm.flags[i] = 0;
   if (tid == 0) sm.nlist = 0;
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
@@ -370,7 +372,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   // out-of-frame positions too (from clamped inputs); S there is
   // overwritten by the edge fill, med3 there is not stored.
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
-  constexpr int M_BW = 8, M_BH = 2, M_UX = TW / M_BW, M_UY = TH / M_BH;
+  constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
   constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
   static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && TW % M_BW == 0 && TH % M_BH == 0,
                 "block tiling");
@@ -398,7 +400,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
         }
     } else {
       const int m = u - S_UNITS;
-      const int ly0 = (m / M_UX) * M_BH, lx0 = (m % M_UX) * M_BW;
+      const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
       float v[(M_BH + 2) * P];
 #pragma unroll
@@ -408,14 +410,10 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
       float m3[M_BH * M_BW];
       blk_med3_8x2<float>(v, m3);
 #pragma unroll
-      for (int r = 0; r < M_BH; ++r) {
-        const int gy = oy + ly0 + r;
-        if (gy >= ny) continue;
-        float* dst = f.m3 + (size_t)gy * nx + ox + lx0;
+      for (int r = 0; r < M_BH; ++r)
 #pragma unroll
         for (int cc = 0; cc < M_BW; ++cc)
-          if (ox + lx0 + cc < nx) dst[cc] = m3[r * M_BW + cc];
-      }
+          if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
     }
   }
   __syncthreads();
@@ -426,8 +424,23 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
       if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
       sm.S[i] = sm.S[Reg<2>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
     }
-    __syncthreads();
+    for (int i = tid; i < Reg<3>::N; i += NT) {
+      const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
+      const int gy = oy + ly, gx = ox + lx;
+      if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
+      sm.M3[i] = sm.M3[Reg<3>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+    }
   }
+  // Saturation (the original input at an unflagged pixel) for the tile; after
+  // this the working image is no longer read.
+  for (int i = tid; i < TH * TW; i += NT) {
+    const int c6 = Reg<6>::idx(i / TW, i % TW);
+    sm.flags[i] = (f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel) ? 8 : 0;
+  }
+  if (tid == 0) sm.nlist2 = 0;
+  __syncthreads();
+  float* SpL = sm.X;                                                // S' per S'-list entry
+  uint16_t* list2 = reinterpret_cast<uint16_t*>(sm.X + TH * TW);   // fine-structure list
 
   // S' = S - med5(S), only where S exceeds the lower threshold (elsewhere
   // S' <= S fails every test): compacted list over the tile.
@@ -451,15 +464,38 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     float m;
     med5x5<float>(w, &m);
     const float sp = __fsub_rn(sm.S[c], m);
-    const int gy = oy + ly, gx = ox + lx;
-    const int c6 = Reg<6>::idx(ly, lx);
-    const bool sat = f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel;
+    SpL[j] = sp;
+    const bool sat = (sm.flags[i] & 8) != 0;
     const bool sig = !sat && sp > f.sigclip;
-    sm.flags[i] = (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
-    if (sig) {
-      f.sp[(size_t)gy * nx + gx] = sp;
-      f.np[(size_t)gy * nx + gx] = sm.N[i];
-    }
+    sm.flags[i] |= (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
+  }
+  __syncthreads();
+
+  // Step 5 where S' > sigclip (not saturated): F = max((med3 - med7(med3))/N,
+  // 0.01) and the objlim test S'/F > objlim, from a compacted list.
+  for (unsigned b = 0; b < n; b += NT) {
+    const unsigned j = b + tid;
+    const bool p = j < n && (sm.flags[sm.list[j]] & 1);
+    list_append(p, (uint16_t)j, list2, &sm.nlist2);
+  }
+  __syncthreads();
+  const unsigned n2 = sm.nlist2;
+  for (unsigned t = tid; t < n2; t += NT) {
+    const int j = list2[t];
+    const int i = sm.list[j];
+    const int ly = i / TW, lx = i % TW;
+    const int c3 = Reg<3>::idx(ly, lx);
+    float w[49];
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
+    float m7;
+    med7x7<float>(w, &m7);
+    const float diff = __fsub_rn(sm.M3[c3], m7);
+    float F = f.fnorm ? __fdiv_rn(diff, sm.N[i]) : diff;
+    F = F < 0.01f ? 0.01f : F;
+    if (__fdiv_rn(SpL[j], F) > f.objlim) sm.flags[i] |= 4;
   }
   __syncthreads();
 
@@ -473,14 +509,19 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     const uint8_t fl = ((ox + lx) < nx && gy < ny) ? sm.flags[ly * TW + lx] : 0;
     const unsigned sig = __ballot_sync(0xffffffffu, fl & 1);
     const unsigned lo = __ballot_sync(0xffffffffu, fl & 2);
+    const unsigned cand = __ballot_sync(0xffffffffu, fl & 4);
     const int w = (ox >> 5) + wd;
     if (lane == 0 && gy < ny && w < f.wpr) {
       const size_t q = (size_t)gy * f.wpr + w;
       f.p_sig[q] = sig;
       f.p_lo[q] = lo;
+      f.p_cand[q] = cand;
     }
   }
-  if (tid == 0 && n) atomicAdd(&f.st->n_sprime, (unsigned long long)n);
+  if (tid == 0) {
+    if (n) atomicAdd(&f.st->n_sprime, (unsigned long long)n);
+    if (n2) atomicAdd(&f.st->n_fine, (unsigned long long)n2);
+  }
 }
 
 // MINB: resident CTAs per SM the register allocation is bounded for (the
@@ -500,87 +541,6 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
     if (!iteration_runs(f, k)) continue;
     core_tile(f, k, (int)(item - f.tile_begin), sm);
-    __syncthreads();
-  }
-}
-
-// ---- step 5: the fine-structure (objlim) test where S' > sigclip ----------
-
-struct FineSmem {
-  float M3[Reg<3>::N];     // med3 plane on R3 (clamped)
-  uint32_t sig[TH * TWW];  // sigclip bit-plane words of the tile
-  uint32_t cand[TH * TWW];
-  uint16_t list[TH * TW];
-  unsigned nlist;
-  int any;
-};
-
-// F = max((med3 - med7(med3)) / N, 0.01) and the objlim test S'/F > objlim
-// at the pixels whose sigclip bit is set; writes the tile's candidate words.
-__global__ void __launch_bounds__(NT) fine_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                  unsigned total, int k, unsigned* head) {
-  __shared__ FineSmem sm;
-  __shared__ unsigned s_item;
-  const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) { s_item = atomicAdd(head, 1u); sm.nlist = 0; sm.any = 0; }
-    __syncthreads();
-    const unsigned item = s_item;
-    if (item >= total) break;
-    const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    if (iteration_runs(f, k)) {
-      const int tix = (int)(item - f.tile_begin);
-      const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
-      const int ny = f.ny, nx = f.nx;
-      for (int r = tid; r < TH * TWW; r += NT) {
-        const int gy = oy + r / TWW, w = (ox >> 5) + r % TWW;
-        const uint32_t v = (gy < ny && w < f.wpr) ? __ldg(f.p_sig + (size_t)gy * f.wpr + w) : 0u;
-        sm.sig[r] = v;
-        sm.cand[r] = 0u;
-        if (v) sm.any = 1;
-      }
-      __syncthreads();
-      if (sm.any) {
-#pragma unroll 4
-        for (int i = tid; i < Reg<3>::N; i += NT) {
-          const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
-          const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
-          sm.M3[i] = __ldg(f.m3 + (size_t)gy * nx + gx);
-        }
-        for (int b = 0; b < TH * TW; b += NT) {
-          const int i = b + tid;
-          const int ly = i / TW, lx = i % TW;
-          const bool p = (sm.sig[ly * TWW + (lx >> 5)] >> (lx & 31)) & 1u;
-          list_append(p, (uint16_t)i, sm.list, &sm.nlist);
-        }
-        __syncthreads();
-        const unsigned n = sm.nlist;
-        for (unsigned j = tid; j < n; j += NT) {
-          const int i = sm.list[j];
-          const int ly = i / TW, lx = i % TW;
-          const int c3 = Reg<3>::idx(ly, lx);
-          float w[49];
-#pragma unroll
-          for (int a = 0; a < 7; ++a)
-#pragma unroll
-            for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
-          float m7;
-          med7x7<float>(w, &m7);
-          const float diff = __fsub_rn(sm.M3[c3], m7);
-          const size_t q = (size_t)(oy + ly) * nx + ox + lx;
-          float F = f.fnorm ? __fdiv_rn(diff, __ldg(f.np + q)) : diff;
-          F = F < 0.01f ? 0.01f : F;
-          const float sp = __ldg(f.sp + q);
-          if (__fdiv_rn(sp, F) > f.objlim) atomicOr(&sm.cand[ly * TWW + (lx >> 5)], 1u << (lx & 31));
-        }
-        if (tid == 0 && n) atomicAdd(&f.st->n_fine, (unsigned long long)n);
-        __syncthreads();
-      }
-      for (int r = tid; r < TH * TWW; r += NT) {
-        const int gy = oy + r / TWW, w = (ox >> 5) + r % TWW;
-        if (gy < ny && w < f.wpr) f.p_cand[(size_t)gy * f.wpr + w] = sm.cand[r];
-      }
-    }
     __syncthreads();
   }
 }

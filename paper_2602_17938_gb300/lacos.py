@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int),
-                ("core_ms", ctypes.c_float * MAX_NITER), ("fine_ms", ctypes.c_float * MAX_NITER),
+                ("core_ms", ctypes.c_float * MAX_NITER),
                 ("grow_ms", ctypes.c_float * MAX_NITER),
                 ("final_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
                 ("n_sprime", ctypes.c_longlong), ("n_fine", ctypes.c_longlong),
@@ -234,8 +234,7 @@ class Context:
         if rc != OK:
             raise LacosError(rc, "lacos_last_profile")
         n = p.n_levels
-        return {"core_ms": list(p.core_ms[:n]),
-                "fine_ms": list(p.fine_ms[:n]), "grow_ms": list(p.grow_ms[:n]),
+        return {"core_ms": list(p.core_ms[:n]), "grow_ms": list(p.grow_ms[:n]),
                 "final_ms": p.final_ms,
                 "px_iterations": p.px_iterations, "n_sprime": p.n_sprime, "n_fine": p.n_fine,
                 "n_replace": p.n_replace, "n_replace_wide": p.n_replace_wide}

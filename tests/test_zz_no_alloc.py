@@ -59,8 +59,9 @@ def test_static_entry_point_rejects_oversize_frames():
         pytest.skip("no CUDA device")
     from paper_2602_17938_gb300 import build, lacos
     build.build()
-    ny, nx = 4096, 2048  # about 101 MiB of scratch > 64 MiB
-    d = torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+    ny, nx = 12000, 12000  # about 86 MiB of scratch > 64 MiB
+    assert lacos.load_library().lacos_scratch_bytes(ny, nx) > lacos.STATIC_SCRATCH_BYTES
+    d = torch.zeros((ny, nx), dtype=torch.uint16, device="cuda")
     m = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
     c = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
     with pytest.raises(lacos.LacosError) as e:
