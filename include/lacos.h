@@ -26,7 +26,7 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (5 bits per pixel plus a few kilobytes per request),
+ * its scratch (5 bits per pixel plus 256 KiB per frame),
  * charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values

@@ -31,6 +31,7 @@ using namespace lacos;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kNtabBytes = 65536 * sizeof(float);  // N per uint16 med5 value
 // Tile-queue heads: one per (kernel, level) plus the final replace.
 constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
 constexpr int kHeadCore = 0;
@@ -95,7 +96,7 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 5 * maskbuf_bytes(f.ny, f.nx);  // M buffers 0/1, planes sig/lo/cand
+    off += 5 * maskbuf_bytes(f.ny, f.nx) + kNtabBytes;  // M 0/1, sig/lo/cand, N table
   }
   L.total = off;
   return L;
@@ -195,6 +196,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_sig = (uint32_t*)(d + L.mask_off[i] + 2 * mb);
     h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
+    h.ntab = (float*)(d + L.mask_off[i] + 5 * mb);
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -244,6 +246,8 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     if (prof) CK(cudaEventRecord(sl.prof_ev[i], s));
     return LACOS_OK;
   };
+  ntab_kernel<<<dim3(256, nf), 256, 0, s>>>(ddesc, nf);
+  CK(cudaGetLastError());
   for (int k = 1; k <= max_niter; ++k) {
     kCoreVariants[cv]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
     CK(cudaGetLastError());
@@ -636,7 +640,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const size_t off_desc = align_up(sizeof(unsigned) * kHeads);
   const size_t off_state = off_desc + align_up(sizeof(FrameDesc));
   const size_t off_masks = off_state + align_up(sizeof(FrameState));
-  const size_t need = off_masks + 5 * mb;
+  const size_t need = off_masks + 5 * mb + kNtabBytes;
   if (need > (size_t)LACOS_STATIC_SCRATCH_BYTES) return LACOS_ENOMEM;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LACOS_ECUDA;
@@ -661,6 +665,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.p_sig = (uint32_t*)(planes + 2 * mb);
   h.p_lo = (uint32_t*)(planes + 3 * mb);
   h.p_cand = (uint32_t*)(planes + 4 * mb);
+  h.ntab = (float*)(planes + 5 * mb);
   h.mask_out = d_mask;
   h.clean_out = d_clean;
   h.st = dstate;
@@ -694,6 +699,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
   const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
+  ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   for (int k = 1; k <= p->niter; ++k) {
     kCoreVariants[sd->core_variant]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, 1, total, k,
                                                                        heads + kHeadCore + k);

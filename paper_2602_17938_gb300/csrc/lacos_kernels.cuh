@@ -72,6 +72,7 @@ struct FrameDesc {
   uint32_t* p_sig;   // bit-planes of the current iteration (ny x wpr words each)
   uint32_t* p_lo;
   uint32_t* p_cand;
+  float* ntab;       // uint16 frames: N for every integer med5 value 0..65535
   uint8_t* mask_out;
   float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
@@ -297,6 +298,16 @@ __device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
   return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
 }
 
+// N for every integer med5 value of a uint16 frame (the same arithmetic as
+// noise_of, evaluated once per value instead of once per pixel).
+__global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
+  const int fi = blockIdx.y;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fi >= nframes || m > 65535) return;
+  const FrameDesc& f = fr[fi];
+  if (f.dtype == 1) f.ntab[m] = noise_of(f, (float)m);
+}
+
 __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, float rt) {
   const float vv = __fadd_rn(vc, vc);
   float c1 = __fsub_rn(__fsub_rn(vv, up), lf);
@@ -329,17 +340,27 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   // flagged pixels (a compacted list; reads touch unflagged pixels only, so
   // it is done in place).
   if (k > 1) {
-    for (int b = 0; b < Reg<4>::N; b += NT) {
-      const int i = b + tid;
-      bool p = false;
-      int c = 0;
-      if (i < Reg<4>::N) {
-        const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
-        const int gy = oy + ly, gx = ox + lx;
-        c = Reg<6>::idx(ly, lx);
-        p = gy >= 0 && gy < ny && gx >= 0 && gx < nx && sm.Mb[c];
+    // The flagged pixels of R4 straight from the staged mask words: one
+    // (row, word) pair per thread.
+    const int cx0 = max(0, ox - 4), cx1 = min(nx, ox + TW + 4);
+    const int w0 = clampi(ox - 6, 0, nx - 1) >> 5;
+    for (int i = tid; i < (TH + 8) * MWORDS; i += NT) {
+      const int ly = i / MWORDS - 4, j = i % MWORDS;
+      const int gy = oy + ly;
+      if (gy < 0 || gy >= ny) continue;
+      const int wbase = (w0 + j) * 32;
+      uint32_t bits = sm.Mw[ly + 6][j];
+      const int lo = cx0 - wbase, hi = cx1 - wbase;  // keep bits b with lo <= b < hi
+      if (hi <= 0 || lo >= 32) continue;
+      if (lo > 0) bits &= 0xffffffffu << lo;
+      if (hi < 32) bits &= (1u << hi) - 1u;
+      if (!bits) continue;
+      unsigned pos = atomicAdd(&sm.nlist, (unsigned)__popc(bits));
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        sm.list[pos++] = (uint16_t)Reg<6>::idx(ly, wbase + b - ox);
       }
-      list_append(p, (uint16_t)c, sm.list, &sm.nlist);
     }
     __syncthreads();
     const unsigned n = sm.nlist;
@@ -393,7 +414,8 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
         for (int cc = 0; cc < S_BW; ++cc) {
           const int q = (r + 2) * P + cc + 2;
           const float L = lplus(v[q], v[q - P], v[q + P], v[q - 1], v[q + 1]);
-          const float N = noise_of(f, m5[r * S_BW + cc]);
+          const float m = m5[r * S_BW + cc];
+          const float N = f.dtype == 1 ? __ldg(f.ntab + __float2int_rz(m)) : noise_of(f, m);
           sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
           const int ty = ly0 + r, tx = lx0 + cc;
           if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.N[ty * TW + tx] = N;

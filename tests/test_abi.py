@@ -38,8 +38,9 @@ def test_host_only_entry_points(lib):
     lib.lacos_scratch_bytes.restype = ctypes.c_size_t
     lib.lacos_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
     n = lib.lacos_scratch_bytes(6388, 9576)
-    # five bit-planes (two mask buffers, three test planes): 5 * 6388 * ceil(9576/32) * 4
-    expect = 5 * 6388 * 300 * 4
+    # five bit-planes (two mask buffers, three test planes): 5 * 6388 * ceil(9576/32) * 4,
+    # and the 65536-entry float table of N per uint16 med5 value
+    expect = 5 * 6388 * 300 * 4 + 65536 * 4
     assert expect <= n < expect + (1 << 20)
     assert lib.lacos_scratch_bytes(0, 5) == 0
 
