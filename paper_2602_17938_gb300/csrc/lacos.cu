@@ -249,7 +249,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   ntab_kernel<<<dim3(256, nf), 256, 0, s>>>(ddesc, nf);
   CK(cudaGetLastError());
   for (int k = 1; k <= max_niter; ++k) {
-    kCoreVariants[cv]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
+    kCoreVariants[cv]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
     CK(cudaGetLastError());
     if (int rc = mark(2 * k - 1)) return rc;
     grow_kernel<<<gw, NT, 0, s>>>(ddesc, nf, total_words, k);
@@ -411,10 +411,10 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
     e = cudaFuncSetAttribute(kCoreVariants[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(CoreSmem));
+                             (int)kCoreSmemBytes);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[v], kCoreVariants[v],
-                                                        NT, sizeof(CoreSmem));
+                                                        NT, kCoreSmemBytes);
     c->blocks_per_sm_core_v[v] = std::max(1, c->blocks_per_sm_core_v[v]);
   }
   if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
@@ -611,10 +611,10 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
     e = cudaDeviceGetAttribute(&sd.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kCoreVariants[sd.core_variant],
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CoreSmem));
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core, kCoreVariants[sd.core_variant],
-                                                        NT, sizeof(CoreSmem));
+                                                        NT, kCoreSmemBytes);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, NT, 0);
     if (e != cudaSuccess) return e;
@@ -701,7 +701,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   for (int k = 1; k <= p->niter; ++k) {
-    kCoreVariants[sd->core_variant]<<<gd, NT, sizeof(CoreSmem), s>>>(ddesc, 1, total, k,
+    kCoreVariants[sd->core_variant]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, 1, total, k,
                                                                        heads + kHeadCore + k);
     grow_kernel<<<gw, NT, 0, s>>>(ddesc, 1, total_words, k);
   }

@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/lacos.h"
 
 namespace lacos_net {
@@ -41,6 +43,23 @@ template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_
 
 __device__ __forceinline__ float MN(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ float MX(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ int MN(int a, int b) { return min(a, b); }
+__device__ __forceinline__ int MX(int a, int b) { return max(a, b); }
+
+// Two 16-bit keys per register: one min/max instruction compares both halves.
+struct U16x2 {
+  uint32_t v;
+};
+__device__ __forceinline__ U16x2 MN(U16x2 a, U16x2 b) {
+  U16x2 r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r.v) : "r"(a.v), "r"(b.v));
+  return r;
+}
+__device__ __forceinline__ U16x2 MX(U16x2 a, U16x2 b) {
+  U16x2 r;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(r.v) : "r"(a.v), "r"(b.v));
+  return r;
+}
 
 #include "networks.cuh"
 
@@ -193,12 +212,34 @@ __device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* l
   if (pred) lst[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
+// Selection keys of the working-image types: float values are their own
+// keys (finite, -0 canonicalised) with -inf/+inf as sentinels; uint16 values
+// become int keys with -1 and 65536 as sentinels.
+template <class XT> struct KeyOf;
+template <> struct KeyOf<float> {
+  using K = float;
+  static __device__ __forceinline__ K lo() { return lacos_net::neg_inf<float>(); }
+  static __device__ __forceinline__ K hi() { return lacos_net::pos_inf<float>(); }
+  static __device__ __forceinline__ K key(float x) { return x; }
+  static __device__ __forceinline__ float back(K k) { return k; }
+};
+template <> struct KeyOf<uint16_t> {
+  using K = int;
+  static __device__ __forceinline__ K lo() { return -1; }
+  static __device__ __forceinline__ K hi() { return 65536; }
+  static __device__ __forceinline__ K key(uint16_t x) { return (int)x; }
+  static __device__ __forceinline__ uint16_t back(K k) { return (uint16_t)k; }
+};
+
 // Masked 5x5 median at shared-memory index c of X (pitch P) with flags Mb:
 // the lower median of the unflagged members.  Flagged members are replaced
-// by sentinels, the first (12 - (n-1)/2) by -inf and the rest by +inf, so
-// that the rank-12 element of the 25 is the rank-(n-1)/2 unflagged value.
-// Returns false when no member is unflagged.
-__device__ __forceinline__ bool maskmed5(const float* X, const uint8_t* Mb, int P, int c, float& out) {
+// by sentinels, the first (12 - (n-1)/2) by the low sentinel and the rest by
+// the high one, so that the rank-12 element of the 25 is the rank-(n-1)/2
+// unflagged value.  Returns false when no member is unflagged.
+template <class XT>
+__device__ __forceinline__ bool maskmed5(const XT* X, const uint8_t* Mb, int P, int c, XT& out) {
+  using KT = KeyOf<XT>;
+  using K = typename KT::K;
   int n = 0;
 #pragma unroll
   for (int dy = -2; dy <= 2; ++dy)
@@ -206,7 +247,7 @@ __device__ __forceinline__ bool maskmed5(const float* X, const uint8_t* Mb, int 
     for (int dx = -2; dx <= 2; ++dx) n += Mb[c + dy * P + dx] ? 0 : 1;
   if (n == 0) return false;
   const int plo = 12 - (n - 1) / 2;
-  float v[25];
+  K v[25];
   int seen = 0;
 #pragma unroll
   for (int dy = -2; dy <= 2; ++dy)
@@ -214,17 +255,22 @@ __device__ __forceinline__ bool maskmed5(const float* X, const uint8_t* Mb, int 
     for (int dx = -2; dx <= 2; ++dx) {
       const int q = c + dy * P + dx;
       const bool fl = Mb[q] != 0;
-      const float s = (seen < plo) ? lacos_net::neg_inf<float>() : lacos_net::pos_inf<float>();
+      const K s = (seen < plo) ? KT::lo() : KT::hi();
       seen += fl ? 1 : 0;
-      v[(dy + 2) * 5 + dx + 2] = fl ? s : X[q];
+      v[(dy + 2) * 5 + dx + 2] = fl ? s : KT::key(X[q]);
     }
-  med5x5<float>(v, &out);
+  K o;
+  med5x5<K>(v, &o);
+  out = KT::back(o);
   return true;
 }
 
 // Masked 7x7 median (the first widening): the same sentinel scheme with the
 // rank-24 element of 49.  Returns false when no member is unflagged.
-__device__ __forceinline__ bool maskmed7(const float* X, const uint8_t* Mb, int P, int c, float& out) {
+template <class XT>
+__device__ __forceinline__ bool maskmed7(const XT* X, const uint8_t* Mb, int P, int c, XT& out) {
+  using KT = KeyOf<XT>;
+  using K = typename KT::K;
   int n = 0;
 #pragma unroll
   for (int dy = -3; dy <= 3; ++dy)
@@ -232,7 +278,7 @@ __device__ __forceinline__ bool maskmed7(const float* X, const uint8_t* Mb, int 
     for (int dx = -3; dx <= 3; ++dx) n += Mb[c + dy * P + dx] ? 0 : 1;
   if (n == 0) return false;
   const int plo = 24 - (n - 1) / 2;
-  float v[49];
+  K v[49];
   int seen = 0;
 #pragma unroll
   for (int dy = -3; dy <= 3; ++dy)
@@ -240,11 +286,13 @@ __device__ __forceinline__ bool maskmed7(const float* X, const uint8_t* Mb, int 
     for (int dx = -3; dx <= 3; ++dx) {
       const int q = c + dy * P + dx;
       const bool fl = Mb[q] != 0;
-      const float s = (seen < plo) ? lacos_net::neg_inf<float>() : lacos_net::pos_inf<float>();
+      const K s = (seen < plo) ? KT::lo() : KT::hi();
       seen += fl ? 1 : 0;
-      v[(dy + 3) * 7 + dx + 3] = fl ? s : X[q];
+      v[(dy + 3) * 7 + dx + 3] = fl ? s : KT::key(X[q]);
     }
-  med7x7<float>(v, &out);
+  K o;
+  med7x7<K>(v, &o);
+  out = KT::back(o);
   return true;
 }
 
@@ -252,28 +300,12 @@ __device__ __forceinline__ bool maskmed7(const float* X, const uint8_t* Mb, int 
 
 constexpr int MWORDS = (TW + 12 + 31) / 32 + 1;  // mask words spanning R6 columns
 
-struct CoreSmem {
-  float X[Reg<6>::N];        // X0 on R6, then the working image I_{k-1} on R4
-  uint8_t Mb[Reg<6>::N];     // M_{k-1} on R6
-  uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
-  float S[Reg<2>::N];        // S on R2
-  float N[TH * TW];          // N on the tile
-  float M3[Reg<3>::N];       // med3(I) on R3
-  uint16_t list[Reg<4>::N];  // work lists (replacement on R4, then S' on the tile)
-  uint8_t flags[TH * TW];    // bit0: S' > sigclip, bit1: S' > lo (both not saturated),
-                             // bit2: candidate, bit3: saturated
-  unsigned nlist, nlist2;
-};
-// Once the dense part is done the working image is dead; its storage then
-// holds S' of the S' list entries and the fine-structure work list.
-static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * Reg<6>::N,
-              "S' and the second list must fit in the working-image storage");
 
 // Stages X0 and the mask M (clamped coordinates) on region H of a tile:
 // X (Reg<H>-indexed floats), Mb (bytes), via the mask words of the rows.
-template <int H>
+template <int H, class XT>
 __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t* M, int oy, int ox,
-                                              float* X, uint8_t* Mb, uint32_t (*Mw)[MWORDS],
+                                              XT* X, uint8_t* Mb, uint32_t (*Mw)[MWORDS],
                                               bool& bad) {
   const int ny = f.ny, nx = f.nx;
   const int w0 = clampi(ox - H, 0, nx - 1) >> 5;
@@ -287,7 +319,10 @@ __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t
   for (int i = threadIdx.x; i < Reg<H>::N; i += NT) {
     const int ly = i / Reg<H>::W - H, lx = i % Reg<H>::W - H;
     const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
-    X[i] = load_x0(f, gy, gx, bad);
+    if constexpr (std::is_same<XT, float>::value)
+      X[i] = load_x0(f, gy, gx, bad);
+    else
+      X[i] = __ldg((const unsigned short*)f.x0 + (size_t)gy * nx + gx);
     Mb[i] = (uint8_t)((Mw[ly + H][(gx >> 5) - w0] >> (gx & 31)) & 1u);
   }
 }
@@ -321,7 +356,179 @@ __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, f
   return __fmul_rn(__fadd_rn(__fadd_rn(c1, c2), __fadd_rn(c3, c4)), 0.25f);
 }
 
-__device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
+// Shared memory of one core tile, by working-image type.  Once the dense
+// part is done the working image is dead; its storage then holds what the
+// later phases need (see spl() and list2()).
+template <class XT> struct CoreSmemT;
+template <> struct CoreSmemT<float> {
+  float X[Reg<6>::N];            // X0 on R6, then the working image I_{k-1} on R4
+  uint8_t Mb[Reg<6>::N];         // M_{k-1} on R6
+  uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
+  float S[Reg<2>::N];            // S on R2
+  float N[TH * TW];              // N on the tile
+  float M3[Reg<3>::N];           // med3(I) on R3
+  uint16_t list[Reg<4>::N];      // work lists (replacement on R4, then S' on the tile)
+  uint8_t flags[TH * TW];        // bit0: S' > sigclip, bit1: S' > lo (both not saturated),
+                                 // bit2: candidate, bit3: saturated
+  unsigned nlist, nlist2;
+  __device__ float* spl() { return X; }                                    // S' per list entry
+  __device__ uint16_t* list2() { return reinterpret_cast<uint16_t*>(X + TH * TW); }
+};
+template <> struct CoreSmemT<uint16_t> {
+  uint16_t X[Reg<6>::N];         // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
+  uint8_t Mb[Reg<6>::N];
+  uint32_t Mw[TH + 12][MWORDS];
+  float S[Reg<2>::N];
+  uint16_t M5[TH * TW];          // med5(I) on the tile: N = table[med5]
+  uint16_t M3[Reg<3>::N];
+  uint16_t list[Reg<4>::N];
+  uint8_t flags[TH * TW];
+  float SpL[TH * TW];
+  unsigned nlist, nlist2;
+  __device__ float* spl() { return SpL; }
+  __device__ uint16_t* list2() { return X; }
+};
+static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * Reg<6>::N,
+              "S' and the second list must fit in the float working-image storage");
+static_assert(TH * TW <= Reg<6>::N, "the second list must fit in the uint16 working-image storage");
+constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<float>) > sizeof(CoreSmemT<uint16_t>)
+                                      ? sizeof(CoreSmemT<float>) : sizeof(CoreSmemT<uint16_t>);
+
+__device__ __forceinline__ U16x2 pack2(uint16_t lo, uint16_t hi) {
+  return U16x2{(uint32_t)lo | ((uint32_t)hi << 16)};
+}
+__device__ __forceinline__ int half_of(U16x2 p, int h) { return h ? (int)(p.v >> 16) : (int)(p.v & 0xffffu); }
+
+// L+ of integer-valued pixels: every intermediate of the float definition is
+// an integer below 2^24, so this integer form gives the same float.
+__device__ __forceinline__ float lplus_int(int vc, int up, int dn, int lf, int rt) {
+  const int vv = vc + vc;
+  const int c1 = max(vv - up - lf, 0), c2 = max(vv - up - rt, 0);
+  const int c3 = max(vv - dn - lf, 0), c4 = max(vv - dn - rt, 0);
+  return __fmul_rn((float)((c1 + c2) + (c3 + c4)), 0.25f);
+}
+
+// Dense part for float32 frames: S on R2 by 4x2 med5 blocks (N kept on the
+// tile), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
+// positions (from clamped inputs); those are overwritten by the edge fill.
+__device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& sm) {
+  constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
+  constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
+  constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
+  static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && (TH + 6) % M_BH == 0, "block tiling");
+  for (int u = threadIdx.x; u < ALL_UNITS; u += NT) {
+    if (u < S_UNITS) {
+      const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
+      constexpr int P = S_BW + 4;
+      float v[(S_BH + 4) * P];
+#pragma unroll
+      for (int a = 0; a < S_BH + 4; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)];
+      float m5[S_BH * S_BW];
+      blk_med5_4x2<float>(v, m5);
+#pragma unroll
+      for (int r = 0; r < S_BH; ++r)
+#pragma unroll
+        for (int cc = 0; cc < S_BW; ++cc) {
+          const int q = (r + 2) * P + cc + 2;
+          const float L = lplus(v[q], v[q - P], v[q + P], v[q - 1], v[q + 1]);
+          const float N = noise_of(f, m5[r * S_BW + cc]);
+          sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
+          const int ty = ly0 + r, tx = lx0 + cc;
+          if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.N[ty * TW + tx] = N;
+        }
+    } else {
+      const int m = u - S_UNITS;
+      const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
+      constexpr int P = M_BW + 2;
+      float v[(M_BH + 2) * P];
+#pragma unroll
+      for (int a = 0; a < M_BH + 2; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)];
+      float m3[M_BH * M_BW];
+      blk_med3_8x2<float>(v, m3);
+#pragma unroll
+      for (int r = 0; r < M_BH; ++r)
+#pragma unroll
+        for (int cc = 0; cc < M_BW; ++cc)
+          if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
+    }
+  }
+}
+
+// Dense part for uint16 frames: the same blocks on packed uint16 pairs, two
+// blocks per register -- a block in the upper half of the region with the
+// block the same distance further down -- so each min/max instruction
+// serves two outputs.  L+ in exact integer arithmetic, N from the table.
+__device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t>& sm) {
+  constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_PAIRS = (TH + 4) / S_BH / 2;
+  constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
+  constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW;
+  constexpr int M_PAIRS = ((TH + 6) / M_BH + 1) / 2, M_DY = M_PAIRS * M_BH;
+  constexpr int S_UNITS = S_UX * S_PAIRS, ALL_UNITS = S_UNITS + M_UX * M_PAIRS;
+  static_assert(((TH + 4) / S_BH) % 2 == 0, "S row-pairs pair up");
+  for (int u = threadIdx.x; u < ALL_UNITS; u += NT) {
+    if (u < S_UNITS) {
+      const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
+      constexpr int P = S_BW + 4;
+      U16x2 v[(S_BH + 4) * P];
+#pragma unroll
+      for (int a = 0; a < S_BH + 4; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+          v[a * P + b] = pack2(sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)],
+                               sm.X[Reg<6>::idx(ly0 + S_DY - 2 + a, lx0 - 2 + b)]);
+      U16x2 m5[S_BH * S_BW];
+      blk_med5_4x2<U16x2>(v, m5);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < S_BH; ++r)
+#pragma unroll
+          for (int cc = 0; cc < S_BW; ++cc) {
+            const int q = (r + 2) * P + cc + 2;
+            const float L = lplus_int(half_of(v[q], h), half_of(v[q - P], h), half_of(v[q + P], h),
+                                      half_of(v[q - 1], h), half_of(v[q + 1], h));
+            const int m = half_of(m5[r * S_BW + cc], h);
+            const float N = __ldg(f.ntab + m);
+            const int ty = ly0 + h * S_DY + r, tx = lx0 + cc;
+            sm.S[Reg<2>::idx(ty, tx)] = __fdiv_rn(L, __fadd_rn(N, N));
+            if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.M5[ty * TW + tx] = (uint16_t)m;
+          }
+    } else {
+      const int mu = u - S_UNITS;
+      const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
+      constexpr int P = M_BW + 2;
+      U16x2 v[(M_BH + 2) * P];
+#pragma unroll
+      for (int a = 0; a < M_BH + 2; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+          v[a * P + b] = pack2(sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)],
+                               sm.X[Reg<6>::idx(ly0 + M_DY - 1 + a, lx0 - 1 + b)]);
+      U16x2 m3[M_BH * M_BW];
+      blk_med3_8x2<U16x2>(v, m3);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < M_BH; ++r) {
+          const int ty = ly0 + h * M_DY + r;
+          if (ty >= TH + 3) continue;
+#pragma unroll
+          for (int cc = 0; cc < M_BW; ++cc)
+            if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ty, lx0 + cc)] = (uint16_t)half_of(m3[r * M_BW + cc], h);
+        }
+    }
+  }
+}
+
+template <class XT>
+__device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm) {
+  using KT = KeyOf<XT>;
+  using K = typename KT::K;
+  constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
   const int tid = threadIdx.x;
   const int oy = (tix / f.tiles_x) * TH;
   const int ox = (tix % f.tiles_x) * TW;
@@ -366,10 +573,10 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     const unsigned n = sm.nlist;
     for (unsigned j = tid; j < n; j += NT) {
       const int c = sm.list[j];
-      float v;
+      XT v;
       if (!maskmed5(sm.X, sm.Mb, Reg<6>::W, c, v)) {
         const int ly = c / Reg<6>::W - 6, lx = c % Reg<6>::W - 6;
-        v = maskmed_wide(f, Mp, oy + ly, ox + lx, 3);
+        v = (XT)maskmed_wide(f, Mp, oy + ly, ox + lx, 3);
         atomicAdd(&f.st->n_replace_wide, 1ull);
       }
       sm.X[c] = v;
@@ -387,57 +594,12 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     }
   }
 
-  // Dense part by register blocks sharing column sorts and merges between
-  // neighbouring outputs: S on R2 (4x2 blocks of med5), med3 on the tile
-  // (8x2 blocks) written straight to its plane.  Blocks evaluate
-  // out-of-frame positions too (from clamped inputs); S there is
-  // overwritten by the edge fill, med3 there is not stored.
-  constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
-  constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
-  constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
-  static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && TW % M_BW == 0 && TH % M_BH == 0,
-                "block tiling");
-  for (int u = tid; u < ALL_UNITS; u += NT) {
-    if (u < S_UNITS) {
-      const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
-      constexpr int P = S_BW + 4;
-      float v[(S_BH + 4) * P];
-#pragma unroll
-      for (int a = 0; a < S_BH + 4; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)];
-      float m5[S_BH * S_BW];
-      blk_med5_4x2<float>(v, m5);
-#pragma unroll
-      for (int r = 0; r < S_BH; ++r)
-#pragma unroll
-        for (int cc = 0; cc < S_BW; ++cc) {
-          const int q = (r + 2) * P + cc + 2;
-          const float L = lplus(v[q], v[q - P], v[q + P], v[q - 1], v[q + 1]);
-          const float m = m5[r * S_BW + cc];
-          const float N = f.dtype == 1 ? __ldg(f.ntab + __float2int_rz(m)) : noise_of(f, m);
-          sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
-          const int ty = ly0 + r, tx = lx0 + cc;
-          if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.N[ty * TW + tx] = N;
-        }
-    } else {
-      const int m = u - S_UNITS;
-      const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
-      constexpr int P = M_BW + 2;
-      float v[(M_BH + 2) * P];
-#pragma unroll
-      for (int a = 0; a < M_BH + 2; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)];
-      float m3[M_BH * M_BW];
-      blk_med3_8x2<float>(v, m3);
-#pragma unroll
-      for (int r = 0; r < M_BH; ++r)
-#pragma unroll
-        for (int cc = 0; cc < M_BW; ++cc)
-          if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
-    }
-  }
+  // Dense part: L+, N, S on R2 and med3 on R3 (register blocks of shared
+  // min/max networks).
+  if constexpr (kU16)
+    dense_u16(f, sm);
+  else
+    dense_f32(f, sm);
   __syncthreads();
   if (edge) {
     for (int i = tid; i < Reg<2>::N; i += NT) {
@@ -457,12 +619,12 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
   // this the working image is no longer read.
   for (int i = tid; i < TH * TW; i += NT) {
     const int c6 = Reg<6>::idx(i / TW, i % TW);
-    sm.flags[i] = (f.satlevel > 0.0f && !sm.Mb[c6] && sm.X[c6] >= f.satlevel) ? 8 : 0;
+    sm.flags[i] = (f.satlevel > 0.0f && !sm.Mb[c6] && (float)sm.X[c6] >= f.satlevel) ? 8 : 0;
   }
   if (tid == 0) sm.nlist2 = 0;
   __syncthreads();
-  float* SpL = sm.X;                                                // S' per S'-list entry
-  uint16_t* list2 = reinterpret_cast<uint16_t*>(sm.X + TH * TW);   // fine-structure list
+  float* SpL = sm.spl();          // S' per S'-list entry
+  uint16_t* list2 = sm.list2();   // fine-structure list
 
   // S' = S - med5(S), only where S exceeds the lower threshold (elsewhere
   // S' <= S fails every test): compacted list over the tile.
@@ -507,22 +669,26 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
     const int i = sm.list[j];
     const int ly = i / TW, lx = i % TW;
     const int c3 = Reg<3>::idx(ly, lx);
-    float w[49];
+    K w[49];
 #pragma unroll
     for (int a = 0; a < 7; ++a)
 #pragma unroll
-      for (int b = 0; b < 7; ++b) w[a * 7 + b] = sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)];
-    float m7;
-    med7x7<float>(w, &m7);
-    const float diff = __fsub_rn(sm.M3[c3], m7);
-    float F = f.fnorm ? __fdiv_rn(diff, sm.N[i]) : diff;
+      for (int b = 0; b < 7; ++b) w[a * 7 + b] = KT::key(sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)]);
+    K m7;
+    med7x7<K>(w, &m7);
+    const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
+    float N;
+    if constexpr (kU16)
+      N = __ldg(f.ntab + sm.M5[i]);
+    else
+      N = sm.N[i];
+    float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
     F = F < 0.01f ? 0.01f : F;
     if (__fdiv_rn(SpL[j], F) > f.objlim) sm.flags[i] |= 4;
   }
   __syncthreads();
 
-  // Bit-planes of the tile (bits beyond the frame stay 0); the candidate
-  // plane is written by fine_kernel.
+  // Bit-planes of the tile (bits beyond the frame stay 0).
   const int lane = tid & 31, warp = tid >> 5;
   for (int r = warp; r < TH * TWW; r += NT / 32) {
     const int ly = r / TWW, wd = r % TWW;
@@ -547,12 +713,12 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmem& sm) {
 }
 
 // MINB: resident CTAs per SM the register allocation is bounded for (the
-// variants trade registers, and so spills, against occupancy).
+// variants trade registers, and so spills, against occupancy).  Each tile
+// takes the path of its frame's dtype.
 template <int MINB>
 __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                         unsigned total, int k, unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CoreSmem& sm = *reinterpret_cast<CoreSmem*>(smem_raw);
   __shared__ unsigned s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(head, 1u);
@@ -562,7 +728,10 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
     if (item >= total) break;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
     if (!iteration_runs(f, k)) continue;
-    core_tile(f, k, (int)(item - f.tile_begin), sm);
+    if (f.dtype == 1)
+      core_tile<uint16_t>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<uint16_t>*>(smem_raw));
+    else
+      core_tile<float>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<float>*>(smem_raw));
     __syncthreads();
   }
 }
