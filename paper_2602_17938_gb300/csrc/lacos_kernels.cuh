@@ -427,12 +427,13 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
         for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)];
       float m5[S_BH * S_BW];
       blk_med5_4x2<float>(v, m5);
+      // L+ from shared memory, so the block inputs are dead after the network.
 #pragma unroll
       for (int r = 0; r < S_BH; ++r)
 #pragma unroll
         for (int cc = 0; cc < S_BW; ++cc) {
-          const int q = (r + 2) * P + cc + 2;
-          const float L = lplus(v[q], v[q - P], v[q + P], v[q - 1], v[q + 1]);
+          const int c = Reg<6>::idx(ly0 + r, lx0 + cc);
+          const float L = lplus(sm.X[c], sm.X[c - Reg<6>::W], sm.X[c + Reg<6>::W], sm.X[c - 1], sm.X[c + 1]);
           const float N = noise_of(f, m5[r * S_BW + cc]);
           sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
           const int ty = ly0 + r, tx = lx0 + cc;
@@ -482,15 +483,16 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
                                sm.X[Reg<6>::idx(ly0 + S_DY - 2 + a, lx0 - 2 + b)]);
       U16x2 m5[S_BH * S_BW];
       blk_med5_4x2<U16x2>(v, m5);
+      // L+ from shared memory, so the packed inputs are dead after the network.
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
           for (int cc = 0; cc < S_BW; ++cc) {
-            const int q = (r + 2) * P + cc + 2;
-            const float L = lplus_int(half_of(v[q], h), half_of(v[q - P], h), half_of(v[q + P], h),
-                                      half_of(v[q - 1], h), half_of(v[q + 1], h));
+            const int c = Reg<6>::idx(ly0 + h * S_DY + r, lx0 + cc);
+            const float L = lplus_int(sm.X[c], sm.X[c - Reg<6>::W], sm.X[c + Reg<6>::W], sm.X[c - 1],
+                                      sm.X[c + 1]);
             const int m = half_of(m5[r * S_BW + cc], h);
             const float N = __ldg(f.ntab + m);
             const int ty = ly0 + h * S_DY + r, tx = lx0 + cc;
