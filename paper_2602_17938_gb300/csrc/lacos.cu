@@ -180,6 +180,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   FrameDesc* hdesc = (FrameDesc*)sl.hpinned;
   unsigned total = 0;
   unsigned long long total_words = 0;
+  unsigned total_gblk = 0;
   int max_niter = 0;
   for (size_t i = 0; i < fr.size(); ++i) {
     const FrameReq& f = fr[i];
@@ -219,6 +220,9 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.tile_end = total;
     h.word_begin = total_words;
     total_words += (unsigned long long)f.ny * h.wpr;
+    h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
+    h.gblk_begin = total_gblk;
+    total_gblk += h.gblk_x * (unsigned)((f.ny + GB_H - 1) / GB_H);
     max_niter = std::max(max_niter, f.p.niter);
   }
   CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
@@ -230,7 +234,6 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   const int cv = c->core_variant;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core_v[cv]));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
-  const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
   // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
   // [2n+1] after finalize.
   const int nev = 2 * max_niter + 2;
@@ -252,7 +255,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     kCoreVariants[cv]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
     CK(cudaGetLastError());
     if (int rc = mark(2 * k - 1)) return rc;
-    grow_kernel<<<gw, NT, 0, s>>>(ddesc, nf, total_words, k);
+    grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, nf, total_gblk, k);
     CK(cudaGetLastError());
     if (int rc = mark(2 * k)) return rc;
   }
@@ -686,7 +689,9 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.tile_begin = 0;
   h.tile_end = total;
   h.word_begin = 0;
-  const unsigned long long total_words = (unsigned long long)ny * h.wpr;
+  h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
+  h.gblk_begin = 0;
+  const unsigned total_gblk = h.gblk_x * (unsigned)((ny + GB_H - 1) / GB_H);
 
   // The array keeps the previous call's contents: the descriptor is
   // rewritten, and the queue heads, the state and M_0 are cleared.
@@ -698,12 +703,11 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
     return LACOS_ECUDA;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
-  const unsigned gw = (unsigned)((total_words + NT - 1) / NT);
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   for (int k = 1; k <= p->niter; ++k) {
     kCoreVariants[sd->core_variant]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, 1, total, k,
                                                                        heads + kHeadCore + k);
-    grow_kernel<<<gw, NT, 0, s>>>(ddesc, 1, total_words, k);
+    grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, 1, total_gblk, k);
   }
   finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, 1, total, heads + kHeadFinal);
   if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;

@@ -100,6 +100,7 @@ struct FrameDesc {
   int tiles_x;
   unsigned int tile_begin, tile_end;    // this frame's range in the flattened tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
+  unsigned int gblk_begin, gblk_x;      // growth blocks: this frame's first, blocks per row
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -750,124 +751,164 @@ __device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
   return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
 }
 
+constexpr int GB_H = 32, GB_W = 8;  // growth block: 32 rows x 8 words (one word per thread)
+static_assert(GB_H * GB_W == NT, "one word per thread");
+
+__device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, unsigned b) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].gblk_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Step 6 for a block of 32 rows x 8 words: the candidate words (with a
+// 2-row, 2-word halo) and the first growth g1 = dil3(cand) & sig (1-row,
+// 1-word halo) are staged in shared memory; each thread then forms
+// g2 = dil3(g1) & lo for its word, M_k = M_{k-1} | g2, and counts new flags.
 __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                  unsigned long long total_words, int k) {
-  const unsigned long long gw = (unsigned long long)blockIdx.x * NT + threadIdx.x;
+                                                  unsigned total_blocks, int k) {
+  __shared__ uint32_t C[GB_H + 4][GB_W + 4];
+  __shared__ uint32_t G1[GB_H + 2][GB_W + 2];
+  __shared__ unsigned s_cnt;
+  const int tid = threadIdx.x;
+  const unsigned blk = blockIdx.x;
+  if (blk >= total_blocks) return;
+  const FrameDesc& f = fr[frame_of_gblk(fr, nframes, blk)];
+  if (!iteration_runs(f, k)) return;
+  const unsigned b = blk - f.gblk_begin;
+  const int y0 = (int)(b / (unsigned)f.gblk_x) * GB_H, w0 = (int)(b % (unsigned)f.gblk_x) * GB_W;
+  const int ny = f.ny, wpr = f.wpr;
+  if (tid == 0) s_cnt = 0;
+  for (int i = tid; i < (GB_H + 4) * (GB_W + 4); i += NT) {
+    const int r = i / (GB_W + 4), c = i % (GB_W + 4);
+    C[r][c] = plane_word(f.p_cand, ny, wpr, y0 - 2 + r, w0 - 2 + c);
+  }
+  __syncthreads();
+  for (int i = tid; i < (GB_H + 2) * (GB_W + 2); i += NT) {
+    const int r = i / (GB_W + 2), c = i % (GB_W + 2);
+    uint32_t d = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][c], C[r + a][c + 1], C[r + a][c + 2]);
+    G1[r][c] = d & plane_word(f.p_sig, ny, wpr, y0 - 1 + r, w0 - 1 + c);
+  }
+  __syncthreads();
+  const int ty = tid / GB_W, tx = tid % GB_W;
+  const int y = y0 + ty, w = w0 + tx;
   unsigned cnt = 0;
-  int fi = -1;
-  if (gw < total_words) {
-    fi = frame_of_word(fr, nframes, gw);
-    const FrameDesc& f = fr[fi];
-    if (iteration_runs(f, k)) {
-      const unsigned long long q = gw - f.word_begin;
-      const int y = (int)(q / (unsigned)f.wpr), w = (int)(q % (unsigned)f.wpr);
-      const int ny = f.ny, wpr = f.wpr;
-      uint32_t cand[5][5];
+  if (y < ny && w < wpr) {
+    uint32_t d2 = 0;
 #pragma unroll
-      for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int b = 0; b < 5; ++b) cand[a][b] = plane_word(f.p_cand, ny, wpr, y - 2 + a, w - 2 + b);
-      // g1 = dil3(cand) & sig on rows y-1..y+1 and words w-1..w+1 (exact:
-      // the candidates of words w-2..w+2 are loaded).
-      uint32_t g1[3][3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          uint32_t v = 0;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) v |= hdil(cand[r + a][b], cand[r + a][b + 1], cand[r + a][b + 2]);
-          g1[r][b] = v & plane_word(f.p_sig, ny, wpr, y - 1 + r, w - 1 + b);
-        }
-      uint32_t d2 = 0;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) d2 |= hdil(g1[r][0], g1[r][1], g1[r][2]);
-      const uint32_t g2 = d2 & plane_word(f.p_lo, ny, wpr, y, w);
-      const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
-      uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
-      const uint32_t mp = __ldg(Mp + (size_t)y * wpr + w);
-      Mn[(size_t)y * wpr + w] = mp | g2;
-      cnt = __popc(g2 & ~mp);
-    }
+    for (int a = 0; a < 3; ++a) d2 |= hdil(G1[ty + a][tx], G1[ty + a][tx + 1], G1[ty + a][tx + 2]);
+    const uint32_t g2 = d2 & plane_word(f.p_lo, ny, wpr, y, w);
+    const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
+    uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
+    const uint32_t mp = __ldg(Mp + (size_t)y * wpr + w);
+    Mn[(size_t)y * wpr + w] = mp | g2;
+    cnt = __popc(g2 & ~mp);
   }
-  const int lane = threadIdx.x & 31;
-  const int f0 = __shfl_sync(0xffffffffu, fi, 0);
-  const bool same = __all_sync(0xffffffffu, fi == f0);
-  if (same) {
-    unsigned s = cnt;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && s && f0 >= 0) atomicAdd(&fr[f0].st->fresh[k], (unsigned long long)s);
-  } else if (cnt) {
-    atomicAdd(&fr[fi].st->fresh[k], (unsigned long long)cnt);
-  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((tid & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+  __syncthreads();
+  if (tid == 0 && s_cnt) atomicAdd(&f.st->fresh[k], (unsigned long long)s_cnt);
 }
 
 // ---- output: cleaned frame and uint8 mask of the last mask ----------------
 
-struct FinalSmem {
-  float X[Reg<3>::N];
+template <class XT>
+struct FinalSmemT {
+  XT X[Reg<3>::N];
   uint8_t Mb[Reg<3>::N];
   uint32_t Mw[TH + 6][MWORDS];
   uint16_t list[TH * TW];
   unsigned nlist;
 };
+constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
 
 // cleaned = R(X0, M_run) (the masked median at flagged pixels, X0 elsewhere),
 // mask = M_run as uint8, the flagged count and the iterations run.  The
 // flagged pixels of a tile are compacted into a list, replaced in shared
-// memory, and the tile is then written out coalesced.
+// memory, and the tile is then written out coalesced, four pixels per
+// thread where the row pitch allows 16-byte stores.
+template <class XT>
+__device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
+  const int tid = threadIdx.x;
+  const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
+  const int run = run_of(f);
+  const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
+  bool bad = false;
+  stage_x0_mask<3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
+  if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
+  __syncthreads();
+  for (int b = 0; b < TH * TW; b += NT) {
+    const int i = b + tid;
+    const int ly = i / TW, lx = i % TW;
+    const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[Reg<3>::idx(ly, lx)];
+    list_append(p, (uint16_t)i, sm.list, &sm.nlist);
+  }
+  __syncthreads();
+  const unsigned n = sm.nlist;
+  // In place: reads touch unflagged pixels only, writes flagged ones.
+  for (unsigned j = tid; j < n; j += NT) {
+    const int i = sm.list[j];
+    const int ly = i / TW, lx = i % TW;
+    const int c = Reg<3>::idx(ly, lx);
+    XT v;
+    if (!maskmed5(sm.X, sm.Mb, Reg<3>::W, c, v) && !maskmed7(sm.X, sm.Mb, Reg<3>::W, c, v))
+      v = (XT)maskmed_wide(f, M, oy + ly, ox + lx, 4);
+    sm.X[c] = v;
+  }
+  __syncthreads();
+  const bool vec = (f.nx & 3) == 0;
+  for (int qd = tid; qd < TH * TW / 4; qd += NT) {
+    const int ly = qd / (TW / 4), lx = (qd % (TW / 4)) * 4;
+    const int gy = oy + ly, gx = ox + lx;
+    if (gy >= f.ny || gx >= f.nx) continue;
+    const int c = Reg<3>::idx(ly, lx);
+    const size_t q = (size_t)gy * f.nx + gx;
+    if (vec && gx + 3 < f.nx) {
+      *reinterpret_cast<float4*>(f.clean_out + q) =
+          make_float4((float)sm.X[c], (float)sm.X[c + 1], (float)sm.X[c + 2], (float)sm.X[c + 3]);
+      *reinterpret_cast<uint32_t*>(f.mask_out + q) =
+          (uint32_t)sm.Mb[c] | ((uint32_t)sm.Mb[c + 1] << 8) | ((uint32_t)sm.Mb[c + 2] << 16) |
+          ((uint32_t)sm.Mb[c + 3] << 24);
+    } else {
+      for (int e = 0; e < 4 && gx + e < f.nx; ++e) {
+        f.clean_out[q + e] = (float)sm.X[c + e];
+        f.mask_out[q + e] = sm.Mb[c + e];
+      }
+    }
+  }
+  if (tid == 0) {
+    if (n) atomicAdd(&f.st->flagged, (unsigned long long)n);
+    if (tix == 0) f.st->iters_run = run;
+  }
+}
+
 __global__ void __launch_bounds__(NT, 4) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                          unsigned total, unsigned* head) {
-  __shared__ FinalSmem sm;
+  __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
   __shared__ unsigned s_item;
   const int tid = threadIdx.x;
   for (;;) {
-    if (tid == 0) { s_item = atomicAdd(head, 1u); sm.nlist = 0; }
+    if (tid == 0) s_item = atomicAdd(head, 1u);
     __syncthreads();
     const unsigned item = s_item;
     if (item >= total) break;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
     const int tix = (int)(item - f.tile_begin);
-    const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
-    const int run = run_of(f);
-    const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
-    bool bad = false;
-    stage_x0_mask<3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
-    if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
-    __syncthreads();
-    for (int b = 0; b < TH * TW; b += NT) {
-      const int i = b + tid;
-      const int ly = i / TW, lx = i % TW;
-      const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[Reg<3>::idx(ly, lx)];
-      list_append(p, (uint16_t)i, sm.list, &sm.nlist);
-    }
-    __syncthreads();
-    const unsigned n = sm.nlist;
-    // In place: reads touch unflagged pixels only, writes flagged ones.
-    for (unsigned j = tid; j < n; j += NT) {
-      const int i = sm.list[j];
-      const int ly = i / TW, lx = i % TW;
-      const int c = Reg<3>::idx(ly, lx);
-      float v;
-      if (!maskmed5(sm.X, sm.Mb, Reg<3>::W, c, v) && !maskmed7(sm.X, sm.Mb, Reg<3>::W, c, v))
-        v = maskmed_wide(f, M, oy + ly, ox + lx, 4);
-      sm.X[c] = v;
-    }
-    __syncthreads();
-    for (int i = tid; i < TH * TW; i += NT) {
-      const int ly = i / TW, lx = i % TW;
-      const int gy = oy + ly, gx = ox + lx;
-      if (gy < f.ny && gx < f.nx) {
-        const int c = Reg<3>::idx(ly, lx);
-        const size_t q = (size_t)gy * f.nx + gx;
-        f.clean_out[q] = sm.X[c];
-        f.mask_out[q] = sm.Mb[c];
-      }
-    }
-    if (tid == 0) {
-      if (n) atomicAdd(&f.st->flagged, (unsigned long long)n);
-      if (tix == 0) f.st->iters_run = run;
+    if (f.dtype == 1) {
+      auto& sm = *reinterpret_cast<FinalSmemT<uint16_t>*>(smem);
+      if (tid == 0) sm.nlist = 0;
+      __syncthreads();
+      finalize_tile<uint16_t>(f, tix, sm);
+    } else {
+      auto& sm = *reinterpret_cast<FinalSmemT<float>*>(smem);
+      if (tid == 0) sm.nlist = 0;
+      __syncthreads();
+      finalize_tile<float>(f, tix, sm);
     }
     __syncthreads();
   }
