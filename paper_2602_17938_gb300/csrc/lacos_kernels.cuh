@@ -1,21 +1,22 @@
 // Device code of the L.A.Cosmic detect-and-clean iteration (sm_103a).
 //
-// Iteration k is three kernels:
+// Iteration k is two kernels:
 //   core_kernel: per TH x TW tile, stages the original frame X0 and the
 //     cumulative mask M_{k-1} with a 6-pixel halo and rebuilds the working
 //     image I_{k-1} = R(X0, M_{k-1}) on the tile + 4 (step 7 of the previous
 //     iteration: unflagged pixels keep X0, flagged ones take the masked
 //     median of unflagged X0, so I depends only on X0 and the mask); then
-//     L+, N and S densely on the tile + 2 and med3(I) on the tile (register
-//     blocks of shared min/max networks) and S' = S - med5(S) from a
-//     compacted list of the pixels where S exceeds the lower threshold
-//     (steps 1-4).  It writes the bit-planes S' > sigclip and S' >
-//     sigfrac*sigclip (both excluding saturated pixels), S' and N where S'
-//     exceeds sigclip, and the med3 plane;
-//   fine_kernel: step 5 at the set bits of the sigclip plane: F from the
-//     med3 plane, the objlim test, the candidate bit-plane;
+//     L+, N and S densely on the tile + 2 and med3(I) on the tile + 3
+//     (register blocks of shared min/max networks), S' = S - med5(S) from a
+//     compacted list of the pixels where S exceeds the lower threshold, and
+//     F with the objlim test from a compacted list of the unsaturated pixels
+//     where S' exceeds sigclip (steps 1-5).  It writes three bit-planes:
+//     S' > sigclip and S' > sigfrac*sigclip (both excluding saturated
+//     pixels) and the candidates;
 //   grow_kernel: step 6 on 32-pixel words, M_k = M_{k-1} | g2 and the count
 //     of newly flagged pixels.
+// For uint16 frames N is read from a 65536-entry table of N(med5) built once
+// per request (ntab_kernel), and the dense networks run on packed pairs.
 // finalize_kernel writes the cleaned frame R(X0, M) and the uint8 mask.
 //
 // Every stage evaluates its own array at in-frame positions only and reads
