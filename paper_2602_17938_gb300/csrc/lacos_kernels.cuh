@@ -163,13 +163,20 @@ __device__ float maskmed_wide(const FrameDesc& f, const uint32_t* M, int gy, int
 }
 
 
-template <int H>
+// The tile grown by H rows and C columns on each side, row-major in shared
+// memory; idx(0, 0) is the tile's first pixel.
+template <int H, int C = H>
 struct Reg {
-  static constexpr int W = TW + 2 * H;
+  static constexpr int W = TW + 2 * C;
   static constexpr int Hh = TH + 2 * H;
   static constexpr int N = W * Hh;
-  __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + H); }
+  __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
 };
+// Staged input regions: 8 extra columns on each side (more than the 6 and 3
+// the stencils need) so that every staged row starts on a 16-byte boundary
+// of both the frame and shared memory.
+using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
+using XR3 = Reg<3, 8>;  // finalize
 
 __device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsigned item) {
   int lo = 0, hi = nframes - 1;
@@ -309,17 +316,53 @@ template <int H, class XT>
 __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t* M, int oy, int ox,
                                               XT* X, uint8_t* Mb, uint32_t (*Mw)[MWORDS],
                                               bool& bad) {
+  using R = Reg<H, 8>;
+  constexpr int C = 8;
   const int ny = f.ny, nx = f.nx;
-  const int w0 = clampi(ox - H, 0, nx - 1) >> 5;
+  const int w0 = clampi(ox - C, 0, nx - 1) >> 5;
   for (int i = threadIdx.x; i < (TH + 2 * H) * MWORDS; i += NT) {
     const int r = i / MWORDS, w = w0 + i % MWORDS;
     const int gy = clampi(oy - H + r, 0, ny - 1);
     Mw[r][i % MWORDS] = w < f.wpr ? __ldg(M + (size_t)gy * f.wpr + w) : 0u;
   }
   __syncthreads();
+  // Columns ox-8 .. ox+TW+7 all inside the frame, rows 16-byte aligned:
+  // 16-byte loads of 16 / sizeof(XT) pixels (rows are still clamped).
+  constexpr int V = 16 / (int)sizeof(XT);  // pixels per 16-byte chunk
+  constexpr int CPR = R::W / V;            // chunks per row
+  static_assert(R::W % V == 0 && C % V == 0 && (32 % V) == 0, "chunking");
+  const bool vec = ((reinterpret_cast<uintptr_t>(f.x0) & 15u) == 0) && (nx % V == 0) && ox - C >= 0 &&
+                   ox + TW + C <= nx;
+  if (vec) {
+    for (int i = threadIdx.x; i < (TH + 2 * H) * CPR; i += NT) {
+      const int r = i / CPR, q = i % CPR;
+      const int gy = clampi(oy - H + r, 0, ny - 1);
+      const int gx = ox - C + q * V;
+      const XT* src = static_cast<const XT*>(f.x0) + (size_t)gy * nx + gx;
+      const int c = r * R::W + q * V;
+      const uint32_t bits = Mw[r][(gx >> 5) - w0] >> (gx & 31);
+      if constexpr (std::is_same<XT, float>::value) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(src));
+        float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (!isfinite(e[t])) { bad = true; e[t] = 0.0f; }
+          e[t] = e[t] == 0.0f ? 0.0f : e[t];  // -0 -> +0
+        }
+        *reinterpret_cast<float4*>(X + c) = make_float4(e[0], e[1], e[2], e[3]);
+        // 4 mask bits -> 4 bytes (bit t moves to bit 8t; no carries between them).
+        *reinterpret_cast<uint32_t*>(Mb + c) = ((bits & 0xfu) * 0x00204081u) & 0x01010101u;
+      } else {
+        *reinterpret_cast<uint4*>(X + c) = __ldg(reinterpret_cast<const uint4*>(src));
+        *reinterpret_cast<uint2*>(Mb + c) = make_uint2(((bits & 0xfu) * 0x00204081u) & 0x01010101u,
+                                                       (((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u);
+      }
+    }
+    return;
+  }
 #pragma unroll 4
-  for (int i = threadIdx.x; i < Reg<H>::N; i += NT) {
-    const int ly = i / Reg<H>::W - H, lx = i % Reg<H>::W - H;
+  for (int i = threadIdx.x; i < R::N; i += NT) {
+    const int ly = i / R::W - H, lx = i % R::W - C;
     const int gy = clampi(oy + ly, 0, ny - 1), gx = clampi(ox + lx, 0, nx - 1);
     if constexpr (std::is_same<XT, float>::value)
       X[i] = load_x0(f, gy, gx, bad);
@@ -363,8 +406,8 @@ __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, f
 // later phases need (see spl() and list2()).
 template <class XT> struct CoreSmemT;
 template <> struct CoreSmemT<float> {
-  float X[Reg<6>::N];            // X0 on R6, then the working image I_{k-1} on R4
-  uint8_t Mb[Reg<6>::N];         // M_{k-1} on R6
+  float X[XR6::N];               // X0 on R6, then the working image I_{k-1} on R4
+  uint8_t Mb[XR6::N];            // M_{k-1} on R6
   uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
   float S[Reg<2>::N];            // S on R2
   float N[TH * TW];              // N on the tile
@@ -377,11 +420,11 @@ template <> struct CoreSmemT<float> {
   __device__ uint16_t* list2() { return reinterpret_cast<uint16_t*>(X + TH * TW); }
 };
 template <> struct CoreSmemT<uint16_t> {
-  uint16_t X[Reg<6>::N];         // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
-  uint8_t Mb[Reg<6>::N];
+  uint16_t X[XR6::N];            // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
+  uint8_t Mb[XR6::N];
   uint32_t Mw[TH + 12][MWORDS];
   float S[Reg<2>::N];
-  uint16_t M5[TH * TW];          // med5(I) on the tile: N = table[med5]
+  uint16_t M5[Reg<2>::N];        // med5(I) on R2 (like S): N = table[med5]
   uint16_t M3[Reg<3>::N];
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
@@ -390,9 +433,9 @@ template <> struct CoreSmemT<uint16_t> {
   __device__ float* spl() { return SpL; }
   __device__ uint16_t* list2() { return X; }
 };
-static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * Reg<6>::N,
+static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * XR6::N,
               "S' and the second list must fit in the float working-image storage");
-static_assert(TH * TW <= Reg<6>::N, "the second list must fit in the uint16 working-image storage");
+static_assert(TH * TW <= XR6::N, "the second list must fit in the uint16 working-image storage");
 constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<float>) > sizeof(CoreSmemT<uint16_t>)
                                       ? sizeof(CoreSmemT<float>) : sizeof(CoreSmemT<uint16_t>);
 
@@ -426,7 +469,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 #pragma unroll
       for (int a = 0; a < S_BH + 4; ++a)
 #pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)];
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[XR6::idx(ly0 - 2 + a, lx0 - 2 + b)];
       float m5[S_BH * S_BW];
       blk_med5_4x2<float>(v, m5);
       // L+ from shared memory, so the block inputs are dead after the network.
@@ -434,8 +477,8 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
       for (int r = 0; r < S_BH; ++r)
 #pragma unroll
         for (int cc = 0; cc < S_BW; ++cc) {
-          const int c = Reg<6>::idx(ly0 + r, lx0 + cc);
-          const float L = lplus(sm.X[c], sm.X[c - Reg<6>::W], sm.X[c + Reg<6>::W], sm.X[c - 1], sm.X[c + 1]);
+          const int c = XR6::idx(ly0 + r, lx0 + cc);
+          const float L = lplus(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
           const float N = noise_of(f, m5[r * S_BW + cc]);
           sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
           const int ty = ly0 + r, tx = lx0 + cc;
@@ -449,7 +492,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 #pragma unroll
       for (int a = 0; a < M_BH + 2; ++a)
 #pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)];
+        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[XR6::idx(ly0 - 1 + a, lx0 - 1 + b)];
       float m3[M_BH * M_BW];
       blk_med3_8x2<float>(v, m3);
 #pragma unroll
@@ -481,8 +524,8 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       for (int a = 0; a < S_BH + 4; ++a)
 #pragma unroll
         for (int b = 0; b < P; ++b)
-          v[a * P + b] = pack2(sm.X[Reg<6>::idx(ly0 - 2 + a, lx0 - 2 + b)],
-                               sm.X[Reg<6>::idx(ly0 + S_DY - 2 + a, lx0 - 2 + b)]);
+          v[a * P + b] = pack2(sm.X[XR6::idx(ly0 - 2 + a, lx0 - 2 + b)],
+                               sm.X[XR6::idx(ly0 + S_DY - 2 + a, lx0 - 2 + b)]);
       U16x2 m5[S_BH * S_BW];
       blk_med5_4x2<U16x2>(v, m5);
       // L+ from shared memory, so the packed inputs are dead after the network.
@@ -492,14 +535,14 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
           for (int cc = 0; cc < S_BW; ++cc) {
-            const int c = Reg<6>::idx(ly0 + h * S_DY + r, lx0 + cc);
-            const float L = lplus_int(sm.X[c], sm.X[c - Reg<6>::W], sm.X[c + Reg<6>::W], sm.X[c - 1],
+            const int c = XR6::idx(ly0 + h * S_DY + r, lx0 + cc);
+            const float L = lplus_int(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1],
                                       sm.X[c + 1]);
             const int m = half_of(m5[r * S_BW + cc], h);
             const float N = __ldg(f.ntab + m);
             const int ty = ly0 + h * S_DY + r, tx = lx0 + cc;
             sm.S[Reg<2>::idx(ty, tx)] = __fdiv_rn(L, __fadd_rn(N, N));
-            if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.M5[ty * TW + tx] = (uint16_t)m;
+            sm.M5[Reg<2>::idx(ty, tx)] = (uint16_t)m;
           }
     } else {
       const int mu = u - S_UNITS;
@@ -510,8 +553,8 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       for (int a = 0; a < M_BH + 2; ++a)
 #pragma unroll
         for (int b = 0; b < P; ++b)
-          v[a * P + b] = pack2(sm.X[Reg<6>::idx(ly0 - 1 + a, lx0 - 1 + b)],
-                               sm.X[Reg<6>::idx(ly0 + M_DY - 1 + a, lx0 - 1 + b)]);
+          v[a * P + b] = pack2(sm.X[XR6::idx(ly0 - 1 + a, lx0 - 1 + b)],
+                               sm.X[XR6::idx(ly0 + M_DY - 1 + a, lx0 - 1 + b)]);
       U16x2 m3[M_BH * M_BW];
       blk_med3_8x2<U16x2>(v, m3);
 #pragma unroll
@@ -554,7 +597,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     // The flagged pixels of R4 straight from the staged mask words: one
     // (row, word) pair per thread.
     const int cx0 = max(0, ox - 4), cx1 = min(nx, ox + TW + 4);
-    const int w0 = clampi(ox - 6, 0, nx - 1) >> 5;
+    const int w0 = clampi(ox - 8, 0, nx - 1) >> 5;  // as staged
     for (int i = tid; i < (TH + 8) * MWORDS; i += NT) {
       const int ly = i / MWORDS - 4, j = i % MWORDS;
       const int gy = oy + ly;
@@ -570,7 +613,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
       while (bits) {
         const int b = __ffs(bits) - 1;
         bits &= bits - 1u;
-        sm.list[pos++] = (uint16_t)Reg<6>::idx(ly, wbase + b - ox);
+        sm.list[pos++] = (uint16_t)XR6::idx(ly, wbase + b - ox);
       }
     }
     __syncthreads();
@@ -578,8 +621,8 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     for (unsigned j = tid; j < n; j += NT) {
       const int c = sm.list[j];
       XT v;
-      if (!maskmed5(sm.X, sm.Mb, Reg<6>::W, c, v)) {
-        const int ly = c / Reg<6>::W - 6, lx = c % Reg<6>::W - 6;
+      if (!maskmed5(sm.X, sm.Mb, XR6::W, c, v)) {
+        const int ly = c / XR6::W - 6, lx = c % XR6::W - 8;
         v = (XT)maskmed_wide(f, Mp, oy + ly, ox + lx, 3);
         atomicAdd(&f.st->n_replace_wide, 1ull);
       }
@@ -592,7 +635,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
         const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
         const int gy = oy + ly, gx = ox + lx;
         if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-        sm.X[Reg<6>::idx(ly, lx)] = sm.X[Reg<6>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+        sm.X[XR6::idx(ly, lx)] = sm.X[XR6::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
       }
       __syncthreads();
     }
@@ -622,7 +665,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
   // Saturation (the original input at an unflagged pixel) for the tile; after
   // this the working image is no longer read.
   for (int i = tid; i < TH * TW; i += NT) {
-    const int c6 = Reg<6>::idx(i / TW, i % TW);
+    const int c6 = XR6::idx(i / TW, i % TW);
     sm.flags[i] = (f.satlevel > 0.0f && !sm.Mb[c6] && (float)sm.X[c6] >= f.satlevel) ? 8 : 0;
   }
   if (tid == 0) sm.nlist2 = 0;
@@ -683,7 +726,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
-      N = __ldg(f.ntab + sm.M5[i]);
+      N = __ldg(f.ntab + sm.M5[Reg<2>::idx(ly, lx)]);
     else
       N = sm.N[i];
     float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
@@ -820,8 +863,8 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
 
 template <class XT>
 struct FinalSmemT {
-  XT X[Reg<3>::N];
-  uint8_t Mb[Reg<3>::N];
+  XT X[XR3::N];
+  uint8_t Mb[XR3::N];
   uint32_t Mw[TH + 6][MWORDS];
   uint16_t list[TH * TW];
   unsigned nlist;
@@ -846,7 +889,7 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
   for (int b = 0; b < TH * TW; b += NT) {
     const int i = b + tid;
     const int ly = i / TW, lx = i % TW;
-    const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[Reg<3>::idx(ly, lx)];
+    const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[XR3::idx(ly, lx)];
     list_append(p, (uint16_t)i, sm.list, &sm.nlist);
   }
   __syncthreads();
@@ -855,9 +898,9 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
   for (unsigned j = tid; j < n; j += NT) {
     const int i = sm.list[j];
     const int ly = i / TW, lx = i % TW;
-    const int c = Reg<3>::idx(ly, lx);
+    const int c = XR3::idx(ly, lx);
     XT v;
-    if (!maskmed5(sm.X, sm.Mb, Reg<3>::W, c, v) && !maskmed7(sm.X, sm.Mb, Reg<3>::W, c, v))
+    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v) && !maskmed7(sm.X, sm.Mb, XR3::W, c, v))
       v = (XT)maskmed_wide(f, M, oy + ly, ox + lx, 4);
     sm.X[c] = v;
   }
@@ -867,14 +910,18 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
     const int ly = qd / (TW / 4), lx = (qd % (TW / 4)) * 4;
     const int gy = oy + ly, gx = ox + lx;
     if (gy >= f.ny || gx >= f.nx) continue;
-    const int c = Reg<3>::idx(ly, lx);
+    const int c = XR3::idx(ly, lx);
     const size_t q = (size_t)gy * f.nx + gx;
-    if (vec && gx + 3 < f.nx) {
-      *reinterpret_cast<float4*>(f.clean_out + q) =
-          make_float4((float)sm.X[c], (float)sm.X[c + 1], (float)sm.X[c + 2], (float)sm.X[c + 3]);
-      *reinterpret_cast<uint32_t*>(f.mask_out + q) =
-          (uint32_t)sm.Mb[c] | ((uint32_t)sm.Mb[c + 1] << 8) | ((uint32_t)sm.Mb[c + 2] << 16) |
-          ((uint32_t)sm.Mb[c + 3] << 24);
+    if (vec && gx + 3 < f.nx) {  // c is a multiple of 4: aligned shared-memory reads
+      float4 o;
+      if constexpr (std::is_same<XT, float>::value) {
+        o = *reinterpret_cast<const float4*>(sm.X + c);
+      } else {
+        const uint2 u = *reinterpret_cast<const uint2*>(sm.X + c);
+        o = make_float4((float)(u.x & 0xffffu), (float)(u.x >> 16), (float)(u.y & 0xffffu), (float)(u.y >> 16));
+      }
+      *reinterpret_cast<float4*>(f.clean_out + q) = o;
+      *reinterpret_cast<uint32_t*>(f.mask_out + q) = *reinterpret_cast<const uint32_t*>(sm.Mb + c);
     } else {
       for (int e = 0; e < 4 && gx + e < f.nx; ++e) {
         f.clean_out[q + e] = (float)sm.X[c + e];
