@@ -234,13 +234,20 @@ def flat_median(n):
     return d, [s[(n - 1) // 2]]
 
 
-def emit_function(name, dag, outputs, in_shape, doc):
-    """Emit a __device__ template taking inputs v[...] and writing o[...]."""
-    lines = [f"// {doc}", f"// {count_ops(dag, outputs)} min/max operations.",
-             "template <class K>",
-             f"__device__ __forceinline__ void {name}(const K* __restrict__ v, K* __restrict__ o) {{"]
+def emit_function(name, dag, outputs, in_shape, doc, loader=False):
+    """Emit a __device__ template taking inputs v[...] and writing o[...].
+
+    With ``loader`` the template (named ``<name>_ld``) takes a callable
+    ``ld(i)`` instead of the array and fetches input i just before its first
+    use, so only the inputs the network is working on need registers."""
+    sig = (f"__device__ __forceinline__ void {name}_ld(const LD& ld, K* __restrict__ o) {{" if loader else
+           f"__device__ __forceinline__ void {name}(const K* __restrict__ v, K* __restrict__ o) {{")
+    lines = [f"// {doc}" + (" (inputs fetched at first use)" if loader else ""),
+             f"// {count_ops(dag, outputs)} min/max operations.",
+             "template <class K, class LD>" if loader else "template <class K>", sig]
     ids = live_ops(dag, outputs)
     names = {}
+    in_idx = {}
     for i, nm in enumerate(dag.names):
         if nm[0] == "in":
             lab = nm[1]
@@ -250,20 +257,29 @@ def emit_function(name, dag, outputs, in_shape, doc):
                     idx = idx * dim + k
             else:
                 idx = lab
-            names[i] = f"v[{idx}]"
+            names[i] = f"v{idx}" if loader else f"v[{idx}]"
+            in_idx[i] = idx
+    loaded = set()
 
     def ref(x):
         if x == NEG:
             return "lacos_net::neg_inf<K>()"
         if x == POS:
             return "lacos_net::pos_inf<K>()"
+        if loader and x in in_idx and x not in loaded:
+            loaded.add(x)
+            lines.append(f"  const K v{in_idx[x]} = ld({in_idx[x]});")
         return names[x]
 
     for i in ids:
         k, a, b = dag.names[i]
+        ra, rb = ref(a), ref(b)
         names[i] = f"t{i}"
         fn = "MN" if k == "min" else "MX"
-        lines.append(f"  const K t{i} = {fn}({ref(a)}, {ref(b)});")
+        lines.append(f"  const K t{i} = {fn}({ra}, {rb});")
+    if loader:
+        for o in outputs:
+            ref(o)
     for j, o in enumerate(outputs):
         lines.append(f"  o[{j}] = {ref(o)};")
     lines.append("}")
@@ -431,12 +447,18 @@ HEADER = """// Generated by gen_networks.py -- do not edit.
 """
 
 
+# Networks also emitted in the fetch-at-first-use form.
+LOADER_NETS = ("blk_med5_4x2", "blk_med3_8x2", "med5x5", "med7x7")
+
+
 def main(out_path):
     nets = build_all()
     verify(nets, trials=300)
     parts = [HEADER]
     for name, (dag, outs, shape, doc) in nets.items():
         parts.append(emit_function(name, dag, outs, shape, doc))
+        if name in LOADER_NETS:
+            parts.append(emit_function(name, dag, outs, shape, doc, loader=True))
     text = "\n\n".join(parts) + "\n"
     with open(out_path, "w") as f:
         f.write(text)

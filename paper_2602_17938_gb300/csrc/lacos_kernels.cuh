@@ -465,13 +465,10 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      float v[(S_BH + 4) * P];
-#pragma unroll
-      for (int a = 0; a < S_BH + 4; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[XR6::idx(ly0 - 2 + a, lx0 - 2 + b)];
+      const float* base = sm.X + XR6::idx(ly0 - 2, lx0 - 2);
+      const auto ld = [&](int i) { return base[(i / P) * XR6::W + i % P]; };
       float m5[S_BH * S_BW];
-      blk_med5_4x2<float>(v, m5);
+      blk_med5_4x2_ld<float>(ld, m5);
       // L+ from shared memory, so the block inputs are dead after the network.
 #pragma unroll
       for (int r = 0; r < S_BH; ++r)
@@ -488,13 +485,10 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
       const int m = u - S_UNITS;
       const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      float v[(M_BH + 2) * P];
-#pragma unroll
-      for (int a = 0; a < M_BH + 2; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b) v[a * P + b] = sm.X[XR6::idx(ly0 - 1 + a, lx0 - 1 + b)];
+      const float* base = sm.X + XR6::idx(ly0 - 1, lx0 - 1);
+      const auto ld = [&](int i) { return base[(i / P) * XR6::W + i % P]; };
       float m3[M_BH * M_BW];
-      blk_med3_8x2<float>(v, m3);
+      blk_med3_8x2_ld<float>(ld, m3);
 #pragma unroll
       for (int r = 0; r < M_BH; ++r)
 #pragma unroll
@@ -519,15 +513,13 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      U16x2 v[(S_BH + 4) * P];
-#pragma unroll
-      for (int a = 0; a < S_BH + 4; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b)
-          v[a * P + b] = pack2(sm.X[XR6::idx(ly0 - 2 + a, lx0 - 2 + b)],
-                               sm.X[XR6::idx(ly0 + S_DY - 2 + a, lx0 - 2 + b)]);
+      const uint16_t* base = sm.X + XR6::idx(ly0 - 2, lx0 - 2);
+      const auto ld = [&](int i) {
+        const int o = (i / P) * XR6::W + i % P;
+        return pack2(base[o], base[o + S_DY * XR6::W]);
+      };
       U16x2 m5[S_BH * S_BW];
-      blk_med5_4x2<U16x2>(v, m5);
+      blk_med5_4x2_ld<U16x2>(ld, m5);
       // L+ from shared memory, so the packed inputs are dead after the network.
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -548,15 +540,13 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      U16x2 v[(M_BH + 2) * P];
-#pragma unroll
-      for (int a = 0; a < M_BH + 2; ++a)
-#pragma unroll
-        for (int b = 0; b < P; ++b)
-          v[a * P + b] = pack2(sm.X[XR6::idx(ly0 - 1 + a, lx0 - 1 + b)],
-                               sm.X[XR6::idx(ly0 + M_DY - 1 + a, lx0 - 1 + b)]);
+      const uint16_t* base = sm.X + XR6::idx(ly0 - 1, lx0 - 1);
+      const auto ld = [&](int i) {
+        const int o = (i / P) * XR6::W + i % P;
+        return pack2(base[o], base[o + M_DY * XR6::W]);
+      };
       U16x2 m3[M_BH * M_BW];
-      blk_med3_8x2<U16x2>(v, m3);
+      blk_med3_8x2_ld<U16x2>(ld, m3);
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -687,13 +677,10 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const int i = sm.list[j];
     const int ly = i / TW, lx = i % TW;
     const int c = Reg<2>::idx(ly, lx);
-    float w[25];
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-      for (int b = 0; b < 5; ++b) w[a * 5 + b] = sm.S[c + (a - 2) * Reg<2>::W + (b - 2)];
+    const float* wb = sm.S + c - 2 * Reg<2>::W - 2;
+    const auto ld = [&](int i) { return wb[(i / 5) * Reg<2>::W + i % 5]; };
     float m;
-    med5x5<float>(w, &m);
+    med5x5_ld<float>(ld, &m);
     const float sp = __fsub_rn(sm.S[c], m);
     SpL[j] = sp;
     const bool sat = (sm.flags[i] & 8) != 0;
@@ -716,13 +703,10 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const int i = sm.list[j];
     const int ly = i / TW, lx = i % TW;
     const int c3 = Reg<3>::idx(ly, lx);
-    K w[49];
-#pragma unroll
-    for (int a = 0; a < 7; ++a)
-#pragma unroll
-      for (int b = 0; b < 7; ++b) w[a * 7 + b] = KT::key(sm.M3[c3 + (a - 3) * Reg<3>::W + (b - 3)]);
+    const XT* wb = sm.M3 + c3 - 3 * Reg<3>::W - 3;
+    const auto ld = [&](int i) { return KT::key(wb[(i / 7) * Reg<3>::W + i % 7]); };
     K m7;
-    med7x7<K>(w, &m7);
+    med7x7_ld<K>(ld, &m7);
     const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
