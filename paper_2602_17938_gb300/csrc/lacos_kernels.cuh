@@ -453,8 +453,8 @@ __device__ __forceinline__ float lplus_int(int vc, int up, int dn, int lf, int r
   return __fmul_rn((float)((c1 + c2) + (c3 + c4)), 0.25f);
 }
 
-// Dense part for float32 frames: S on R2 by 4x2 med5 blocks (N kept on the
-// tile), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
+// Dense networks for float32 frames: med5 on R2 by 4x2 blocks (parked in
+// S), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
 // positions (from clamped inputs); those are overwritten by the edge fill.
 __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& sm) {
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
@@ -469,18 +469,11 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
       const auto ld = [&](int i) { return base[(i / P) * XR6::W + i % P]; };
       float m5[S_BH * S_BW];
       blk_med5_4x2_ld<float>(ld, m5);
-      // L+ from shared memory, so the block inputs are dead after the network.
+      // med5 parked in S; dense_pixels turns it into N and S.
 #pragma unroll
       for (int r = 0; r < S_BH; ++r)
 #pragma unroll
-        for (int cc = 0; cc < S_BW; ++cc) {
-          const int c = XR6::idx(ly0 + r, lx0 + cc);
-          const float L = lplus(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
-          const float N = noise_of(f, m5[r * S_BW + cc]);
-          sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = __fdiv_rn(L, __fadd_rn(N, N));
-          const int ty = ly0 + r, tx = lx0 + cc;
-          if (ty >= 0 && ty < TH && tx >= 0 && tx < TW) sm.N[ty * TW + tx] = N;
-        }
+        for (int cc = 0; cc < S_BW; ++cc) sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = m5[r * S_BW + cc];
     } else {
       const int m = u - S_UNITS;
       const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
@@ -501,7 +494,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 // Dense part for uint16 frames: the same blocks on packed uint16 pairs, two
 // blocks per register -- a block in the upper half of the region with the
 // block the same distance further down -- so each min/max instruction
-// serves two outputs.  L+ in exact integer arithmetic, N from the table.
+// serves two outputs.  med5 goes to M5 (it indexes the N table).
 __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t>& sm) {
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_PAIRS = (TH + 4) / S_BH / 2;
   constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
@@ -520,22 +513,13 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       };
       U16x2 m5[S_BH * S_BW];
       blk_med5_4x2_ld<U16x2>(ld, m5);
-      // L+ from shared memory, so the packed inputs are dead after the network.
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
-          for (int cc = 0; cc < S_BW; ++cc) {
-            const int c = XR6::idx(ly0 + h * S_DY + r, lx0 + cc);
-            const float L = lplus_int(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1],
-                                      sm.X[c + 1]);
-            const int m = half_of(m5[r * S_BW + cc], h);
-            const float N = __ldg(f.ntab + m);
-            const int ty = ly0 + h * S_DY + r, tx = lx0 + cc;
-            sm.S[Reg<2>::idx(ty, tx)] = __fdiv_rn(L, __fadd_rn(N, N));
-            sm.M5[Reg<2>::idx(ty, tx)] = (uint16_t)m;
-          }
+          for (int cc = 0; cc < S_BW; ++cc)
+            sm.M5[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = (uint16_t)half_of(m5[r * S_BW + cc], h);
     } else {
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
@@ -558,6 +542,42 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
             if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ty, lx0 + cc)] = (uint16_t)half_of(m3[r * M_BW + cc], h);
         }
     }
+  }
+}
+
+// Per-pixel part of the dense step, spread evenly over the block: L+, N and
+// S = L+/(2N) at every R2 position from the working image and the parked
+// med5; for the tile's in-frame pixels also the saturation flag (the
+// original input at an unflagged pixel) and the S' work list (S above the
+// lower threshold; elsewhere S' <= S fails every test).
+template <class XT>
+__device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& sm, int oy, int ox) {
+  constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
+  for (int b = 0; b < Reg<2>::N; b += NT) {
+    const int i = b + threadIdx.x;
+    bool p = false;
+    int t = 0;
+    if (i < Reg<2>::N) {
+      const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
+      const int c = XR6::idx(ly, lx);
+      float L, N;
+      if constexpr (kU16) {
+        L = lplus_int(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
+        N = __ldg(f.ntab + sm.M5[i]);
+      } else {
+        L = lplus(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
+        N = noise_of(f, sm.S[i]);
+      }
+      const float S = __fdiv_rn(L, __fadd_rn(N, N));
+      sm.S[i] = S;
+      if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
+        t = ly * TW + lx;
+        if constexpr (!kU16) sm.N[t] = N;
+        sm.flags[t] = (f.satlevel > 0.0f && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel) ? 8 : 0;
+        p = (oy + ly) < f.ny && (ox + lx) < f.nx && S > f.thr_min;
+      }
+    }
+    list_append(p, (uint16_t)t, sm.list, &sm.nlist);
   }
 }
 
@@ -631,12 +651,15 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     }
   }
 
-  // Dense part: L+, N, S on R2 and med3 on R3 (register blocks of shared
-  // min/max networks).
+  // Dense part: med5 on R2 and med3 on R3 (register blocks of shared min/max
+  // networks), then L+, N, S, the saturation flags and the S' list per pixel.
   if constexpr (kU16)
     dense_u16(f, sm);
   else
     dense_f32(f, sm);
+  if (tid == 0) sm.nlist2 = 0;
+  __syncthreads();
+  dense_pixels(f, sm, oy, ox);
   __syncthreads();
   if (edge) {
     for (int i = tid; i < Reg<2>::N; i += NT) {
@@ -652,26 +675,12 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
       sm.M3[i] = sm.M3[Reg<3>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
     }
   }
-  // Saturation (the original input at an unflagged pixel) for the tile; after
-  // this the working image is no longer read.
-  for (int i = tid; i < TH * TW; i += NT) {
-    const int c6 = XR6::idx(i / TW, i % TW);
-    sm.flags[i] = (f.satlevel > 0.0f && !sm.Mb[c6] && (float)sm.X[c6] >= f.satlevel) ? 8 : 0;
-  }
-  if (tid == 0) sm.nlist2 = 0;
-  __syncthreads();
+  // The working image is no longer read: its storage holds S' and list2.
   float* SpL = sm.spl();          // S' per S'-list entry
   uint16_t* list2 = sm.list2();   // fine-structure list
 
-  // S' = S - med5(S), only where S exceeds the lower threshold (elsewhere
-  // S' <= S fails every test): compacted list over the tile.
-  for (int b = 0; b < TH * TW; b += NT) {
-    const int i = b + tid;
-    const int ly = i / TW, lx = i % TW;
-    const bool p = (oy + ly) < ny && (ox + lx) < nx && sm.S[Reg<2>::idx(ly, lx)] > f.thr_min;
-    list_append(p, (uint16_t)i, sm.list, &sm.nlist);
-  }
-  __syncthreads();
+  // S' = S - med5(S) at the S'-list pixels.
+  if (edge) __syncthreads();
   const unsigned n = sm.nlist;
   for (unsigned j = tid; j < n; j += NT) {
     const int i = sm.list[j];
