@@ -424,7 +424,7 @@ template <> struct CoreSmemT<uint16_t> {
   uint8_t Mb[XR6::N];
   uint32_t Mw[TH + 12][MWORDS];
   float S[Reg<2>::N];
-  uint16_t M5[Reg<2>::N];        // med5(I) on R2 (like S): N = table[med5]
+  float N2[Reg<2>::N];           // N on R2 (the table at med5(I))
   uint16_t M3[Reg<3>::N];
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
@@ -494,7 +494,8 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 // Dense part for uint16 frames: the same blocks on packed uint16 pairs, two
 // blocks per register -- a block in the upper half of the region with the
 // block the same distance further down -- so each min/max instruction
-// serves two outputs.  med5 goes to M5 (it indexes the N table).
+// serves two outputs.  Each med5 indexes the N table right away (the
+// block's 16 loads are in flight together); N goes to N2.
 __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t>& sm) {
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_PAIRS = (TH + 4) / S_BH / 2;
   constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
@@ -519,7 +520,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
           for (int cc = 0; cc < S_BW; ++cc)
-            sm.M5[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = (uint16_t)half_of(m5[r * S_BW + cc], h);
+            sm.N2[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = __ldg(f.ntab + half_of(m5[r * S_BW + cc], h));
     } else {
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
@@ -547,23 +548,25 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
 
 // Per-pixel part of the dense step, spread evenly over the block: L+, N and
 // S = L+/(2N) at every R2 position from the working image and the parked
-// med5; for the tile's in-frame pixels also the saturation flag (the
-// original input at an unflagged pixel) and the S' work list (S above the
-// lower threshold; elsewhere S' <= S fails every test).
+// med5 (float frames) or N (uint16 frames); for the tile's in-frame pixels
+// also the saturation flag (the original input at an unflagged pixel) and
+// the S' work list (S above the lower threshold; elsewhere S' <= S fails
+// every test).
 template <class XT>
 __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& sm, int oy, int ox) {
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
-  for (int b = 0; b < Reg<2>::N; b += NT) {
-    const int i = b + threadIdx.x;
-    bool p = false;
-    int t = 0;
+  constexpr int IT = (Reg<2>::N + NT - 1) / NT;
+  static_assert(IT <= 32, "one bit per iteration");
+  uint32_t hits = 0;  // bit it: the pixel of iteration it joins the S' list
+  for (int it = 0; it < IT; ++it) {
+    const int i = it * NT + threadIdx.x;
     if (i < Reg<2>::N) {
       const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
       const int c = XR6::idx(ly, lx);
       float L, N;
       if constexpr (kU16) {
         L = lplus_int(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
-        N = __ldg(f.ntab + sm.M5[i]);
+        N = sm.N2[i];
       } else {
         L = lplus(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
         N = noise_of(f, sm.S[i]);
@@ -571,13 +574,31 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
       const float S = __fdiv_rn(L, __fadd_rn(N, N));
       sm.S[i] = S;
       if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
-        t = ly * TW + lx;
+        const int t = ly * TW + lx;
         if constexpr (!kU16) sm.N[t] = N;
         sm.flags[t] = (f.satlevel > 0.0f && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel) ? 8 : 0;
-        p = (oy + ly) < f.ny && (ox + lx) < f.nx && S > f.thr_min;
+        if ((oy + ly) < f.ny && (ox + lx) < f.nx && S > f.thr_min) hits |= 1u << it;
       }
     }
-    list_append(p, (uint16_t)t, sm.list, &sm.nlist);
+  }
+  // One shared-memory atomic per warp: exclusive scan of the lanes' counts.
+  const int lane = threadIdx.x & 31;
+  const unsigned cnt = __popc(hits);
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  unsigned base = 0;
+  if (lane == 31 && incl) base = atomicAdd(&sm.nlist, incl);
+  base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+  while (hits) {
+    const int it = __ffs(hits) - 1;
+    hits &= hits - 1u;
+    const int i = it * NT + threadIdx.x;
+    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
+    sm.list[base++] = (uint16_t)(ly * TW + lx);
   }
 }
 
@@ -719,7 +740,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
-      N = __ldg(f.ntab + sm.M5[Reg<2>::idx(ly, lx)]);
+      N = sm.N2[Reg<2>::idx(ly, lx)];
     else
       N = sm.N[i];
     float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
