@@ -413,8 +413,8 @@ template <> struct CoreSmemT<float> {
   float N[TH * TW];              // N on the tile
   float M3[Reg<3>::N];           // med3(I) on R3
   uint16_t list[Reg<4>::N];      // work lists (replacement on R4, then S' on the tile)
-  uint8_t flags[TH * TW];        // bit0: S' > sigclip, bit1: S' > lo (both not saturated),
-                                 // bit2: candidate, bit3: saturated
+  uint8_t flags[TH * TW];        // bit0: S' > sigclip (not saturated), bit3: saturated
+  uint32_t pw[3][TH][TWW];       // the tile's sig, lo and candidate bit-plane words
   unsigned nlist, nlist2;
   __device__ float* spl() { return X; }                                    // S' per list entry
   __device__ uint16_t* list2() { return reinterpret_cast<uint16_t*>(X + TH * TW); }
@@ -429,6 +429,7 @@ template <> struct CoreSmemT<uint16_t> {
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
   float SpL[TH * TW];
+  uint32_t pw[3][TH][TWW];
   unsigned nlist, nlist2;
   __device__ float* spl() { return SpL; }
   __device__ uint16_t* list2() { return X; }
@@ -614,6 +615,8 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
   const bool edge = (oy - 6 < 0) || (ox - 6 < 0) || (oy + TH + 6 > ny) || (ox + TW + 6 > nx);
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
 
+  for (int i = tid; i < 3 * TH * TWW; i += NT) (&sm.pw[0][0][0])[i] = 0u;
+
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
   bool bad = false;
   stage_x0_mask<6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
@@ -714,8 +717,12 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const float sp = __fsub_rn(sm.S[c], m);
     SpL[j] = sp;
     const bool sat = (sm.flags[i] & 8) != 0;
-    const bool sig = !sat && sp > f.sigclip;
-    sm.flags[i] |= (uint8_t)((sig ? 1 : 0) | ((!sat && sp > f.lo) ? 2 : 0));
+    const uint32_t bit = 1u << (lx & 31);
+    if (!sat && sp > f.sigclip) {
+      sm.flags[i] |= 1;
+      atomicOr(&sm.pw[0][ly][lx >> 5], bit);
+    }
+    if (!sat && sp > f.lo) atomicOr(&sm.pw[1][ly][lx >> 5], bit);
   }
   __syncthreads();
 
@@ -745,26 +752,17 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
       N = sm.N[i];
     float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
     F = F < 0.01f ? 0.01f : F;
-    if (__fdiv_rn(SpL[j], F) > f.objlim) sm.flags[i] |= 4;
+    if (__fdiv_rn(SpL[j], F) > f.objlim) atomicOr(&sm.pw[2][ly][lx >> 5], 1u << (lx & 31));
   }
   __syncthreads();
 
-  // Bit-planes of the tile (bits beyond the frame stay 0).
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int r = warp; r < TH * TWW; r += NT / 32) {
-    const int ly = r / TWW, wd = r % TWW;
-    const int lx = wd * 32 + lane;
-    const int gy = oy + ly;
-    const uint8_t fl = ((ox + lx) < nx && gy < ny) ? sm.flags[ly * TW + lx] : 0;
-    const unsigned sig = __ballot_sync(0xffffffffu, fl & 1);
-    const unsigned lo = __ballot_sync(0xffffffffu, fl & 2);
-    const unsigned cand = __ballot_sync(0xffffffffu, fl & 4);
-    const int w = (ox >> 5) + wd;
-    if (lane == 0 && gy < ny && w < f.wpr) {
-      const size_t q = (size_t)gy * f.wpr + w;
-      f.p_sig[q] = sig;
-      f.p_lo[q] = lo;
-      f.p_cand[q] = cand;
+  // Bit-planes of the tile out (only in-frame pixels ever set a bit).
+  for (int t = tid; t < 3 * TH * TWW; t += NT) {
+    const int pl = t / (TH * TWW), r = (t / TWW) % TH, wd = t % TWW;
+    const int gy = oy + r, w = (ox >> 5) + wd;
+    if (gy < ny && w < f.wpr) {
+      uint32_t* P = pl == 0 ? f.p_sig : (pl == 1 ? f.p_lo : f.p_cand);
+      P[(size_t)gy * f.wpr + w] = sm.pw[pl][r][wd];
     }
   }
   if (tid == 0) {
