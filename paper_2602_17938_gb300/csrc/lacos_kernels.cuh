@@ -170,7 +170,7 @@ struct Reg {
   static constexpr int W = TW + 2 * C;
   static constexpr int Hh = TH + 2 * H;
   static constexpr int N = W * Hh;
-  __device__ static __forceinline__ int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
+  __host__ __device__ static constexpr int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
 };
 // Staged input regions: 8 extra columns on each side (more than the 6 and 3
 // the stencils need) so that every staged row starts on a 16-byte boundary
@@ -454,6 +454,33 @@ __device__ __forceinline__ float lplus_int(int vc, int up, int dn, int lf, int r
   return __fmul_rn((float)((c1 + c2) + (c3 + c4)), 0.25f);
 }
 
+// Block-network inputs from the staged image, 4 aligned pixels per shared
+// load (the network asks for each input once; loads of the same group are
+// merged).  Window column 0 must sit on a 4-pixel boundary of the row.
+template <int P>
+struct QuadLoaderF32 {
+  const float* base;  // window element (0, 0)
+  __device__ __forceinline__ float operator()(int i) const {
+    const int a = i / P, b = i % P;
+    const float4 q = *reinterpret_cast<const float4*>(base + a * XR6::W + (b & ~3));
+    return (b & 3) == 0 ? q.x : (b & 3) == 1 ? q.y : (b & 3) == 2 ? q.z : q.w;
+  }
+};
+// Packed pairs for uint16 frames: low half from the window row, high half
+// from the row DY further down.
+template <int P, int DY>
+struct QuadLoaderU16 {
+  const uint16_t* base;
+  __device__ __forceinline__ U16x2 operator()(int i) const {
+    const int a = i / P, b = i % P;
+    const uint16_t* p = base + a * XR6::W + (b & ~3);
+    const uint2 lo = *reinterpret_cast<const uint2*>(p);
+    const uint2 hi = *reinterpret_cast<const uint2*>(p + DY * XR6::W);
+    const uint32_t l = (b & 2) ? lo.y : lo.x, h = (b & 2) ? hi.y : hi.x;
+    return U16x2{__byte_perm(l, h, (b & 1) ? 0x7632 : 0x5410)};
+  }
+};
+
 // Dense networks for float32 frames: med5 on R2 by 4x2 blocks (parked in
 // S), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
 // positions (from clamped inputs); those are overwritten by the edge fill.
@@ -462,12 +489,16 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
   constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
   constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
   static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && (TH + 6) % M_BH == 0, "block tiling");
+  // Window columns start at lx0 - 2 = 4u - 4 (med5) and lx0 - 1 = 8m - 4
+  // (med3): 4-pixel aligned in the 8-column-halo staging rows; the med3
+  // window's last 4-group reads at most 2 pixels past it, still in the row.
+  static_assert(XR6::W % 4 == 0 && XR6::idx(0, -4) % 4 == 0 && (-3 + 8 * (M_UX - 1)) - 1 + 12 <= TW + 8,
+                "aligned block windows");
   for (int u = threadIdx.x; u < ALL_UNITS; u += NT) {
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      const float* base = sm.X + XR6::idx(ly0 - 2, lx0 - 2);
-      const auto ld = [&](int i) { return base[(i / P) * XR6::W + i % P]; };
+      const QuadLoaderF32<P> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       float m5[S_BH * S_BW];
       blk_med5_4x2_ld<float>(ld, m5);
       // med5 parked in S; dense_pixels turns it into N and S.
@@ -479,8 +510,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
       const int m = u - S_UNITS;
       const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      const float* base = sm.X + XR6::idx(ly0 - 1, lx0 - 1);
-      const auto ld = [&](int i) { return base[(i / P) * XR6::W + i % P]; };
+      const QuadLoaderF32<P> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
       float m3[M_BH * M_BW];
       blk_med3_8x2_ld<float>(ld, m3);
 #pragma unroll
@@ -508,11 +538,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      const uint16_t* base = sm.X + XR6::idx(ly0 - 2, lx0 - 2);
-      const auto ld = [&](int i) {
-        const int o = (i / P) * XR6::W + i % P;
-        return pack2(base[o], base[o + S_DY * XR6::W]);
-      };
+      const QuadLoaderU16<P, S_DY> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       U16x2 m5[S_BH * S_BW];
       blk_med5_4x2_ld<U16x2>(ld, m5);
 #pragma unroll
@@ -526,11 +552,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      const uint16_t* base = sm.X + XR6::idx(ly0 - 1, lx0 - 1);
-      const auto ld = [&](int i) {
-        const int o = (i / P) * XR6::W + i % P;
-        return pack2(base[o], base[o + M_DY * XR6::W]);
-      };
+      const QuadLoaderU16<P, M_DY> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
       U16x2 m3[M_BH * M_BW];
       blk_med3_8x2_ld<U16x2>(ld, m3);
 #pragma unroll
