@@ -401,9 +401,7 @@ __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, f
   return __fmul_rn(__fadd_rn(__fadd_rn(c1, c2), __fadd_rn(c3, c4)), 0.25f);
 }
 
-// Shared memory of one core tile, by working-image type.  Once the dense
-// part is done the working image is dead; its storage then holds what the
-// later phases need (see spl() and list2()).
+// Shared memory of one core tile, by working-image type.
 template <class XT> struct CoreSmemT;
 template <> struct CoreSmemT<float> {
   float X[XR6::N];               // X0 on R6, then the working image I_{k-1} on R4
@@ -412,12 +410,12 @@ template <> struct CoreSmemT<float> {
   float S[Reg<2>::N];            // S on R2
   float N[TH * TW];              // N on the tile
   float M3[Reg<3>::N];           // med3(I) on R3
-  uint16_t list[Reg<4>::N];      // work lists (replacement on R4, then S' on the tile)
-  uint8_t flags[TH * TW];        // bit0: S' > sigclip (not saturated), bit3: saturated
+  uint16_t list[Reg<4>::N];      // work lists: replacement on R4; then fine-structure
+                                 // items from the front and S'-only items from the back
+  uint8_t flags[TH * TW];        // bit3: saturated
   uint32_t pw[3][TH][TWW];       // the tile's sig, lo and candidate bit-plane words
-  unsigned nlist, nlist2;
-  __device__ float* spl() { return X; }                                    // S' per list entry
-  __device__ uint16_t* list2() { return reinterpret_cast<uint16_t*>(X + TH * TW); }
+  unsigned nlist, nlist2;        // list lengths (S'-only, fine-structure)
+  unsigned nfine;                // F evaluations of the tile
 };
 template <> struct CoreSmemT<uint16_t> {
   uint16_t X[XR6::N];            // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
@@ -428,15 +426,11 @@ template <> struct CoreSmemT<uint16_t> {
   uint16_t M3[Reg<3>::N];
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
-  float SpL[TH * TW];
   uint32_t pw[3][TH][TWW];
   unsigned nlist, nlist2;
-  __device__ float* spl() { return SpL; }
-  __device__ uint16_t* list2() { return X; }
+  unsigned nfine;
 };
-static_assert(sizeof(float) * TH * TW + sizeof(uint16_t) * TH * TW <= sizeof(float) * XR6::N,
-              "S' and the second list must fit in the float working-image storage");
-static_assert(TH * TW <= XR6::N, "the second list must fit in the uint16 working-image storage");
+static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list array");
 constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<float>) > sizeof(CoreSmemT<uint16_t>)
                                       ? sizeof(CoreSmemT<float>) : sizeof(CoreSmemT<uint16_t>);
 
@@ -569,18 +563,44 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
   }
 }
 
+// Appends val(it) for every set bit `it` of each lane's `hits` to a shared
+// list with one atomic per warp (an exclusive scan of the lane counts):
+// upward from lst[0] when top < 0, else downward from lst[top].
+template <class V>
+__device__ __forceinline__ void warp_emit(uint32_t hits, unsigned* cnt, uint16_t* lst, int top, V val) {
+  const int lane = threadIdx.x & 31;
+  const unsigned c = __popc(hits);
+  unsigned incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  unsigned base = 0;
+  if (lane == 31 && incl) base = atomicAdd(cnt, incl);
+  base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+  while (hits) {
+    const int it = __ffs(hits) - 1;
+    hits &= hits - 1u;
+    lst[top < 0 ? (int)base : top - (int)base] = val(it);
+    ++base;
+  }
+}
+
 // Per-pixel part of the dense step, spread evenly over the block: L+, N and
 // S = L+/(2N) at every R2 position from the working image and the parked
 // med5 (float frames) or N (uint16 frames); for the tile's in-frame pixels
 // also the saturation flag (the original input at an unflagged pixel) and
-// the S' work list (S above the lower threshold; elsewhere S' <= S fails
-// every test).
+// the two sparse work lists.  Since S' <= S, a test S' > t can only pass
+// where S > t: pixels with S > sigclip (unsaturated) are fine-structure
+// items (S', then F where S' > sigclip), the others with S above the lower
+// threshold are S'-only items; elsewhere every test fails.
 template <class XT>
 __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& sm, int oy, int ox) {
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
   constexpr int IT = (Reg<2>::N + NT - 1) / NT;
   static_assert(IT <= 32, "one bit per iteration");
-  uint32_t hits = 0;  // bit it: the pixel of iteration it joins the S' list
+  uint32_t hits = 0, hits_f = 0;  // bit it: the pixel of iteration it is an S'-only / fine item
   for (int it = 0; it < IT; ++it) {
     const int i = it * NT + threadIdx.x;
     if (i < Reg<2>::N) {
@@ -599,30 +619,23 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
       if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
         const int t = ly * TW + lx;
         if constexpr (!kU16) sm.N[t] = N;
-        sm.flags[t] = (f.satlevel > 0.0f && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel) ? 8 : 0;
-        if ((oy + ly) < f.ny && (ox + lx) < f.nx && S > f.thr_min) hits |= 1u << it;
+        const bool sat = f.satlevel > 0.0f && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
+        sm.flags[t] = sat ? 8 : 0;
+        if ((oy + ly) < f.ny && (ox + lx) < f.nx) {
+          if (!sat && S > f.sigclip)
+            hits_f |= 1u << it;
+          else if (S > f.thr_min)
+            hits |= 1u << it;
+        }
       }
     }
   }
-  // One shared-memory atomic per warp: exclusive scan of the lanes' counts.
-  const int lane = threadIdx.x & 31;
-  const unsigned cnt = __popc(hits);
-  unsigned incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  unsigned base = 0;
-  if (lane == 31 && incl) base = atomicAdd(&sm.nlist, incl);
-  base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
-  while (hits) {
-    const int it = __ffs(hits) - 1;
-    hits &= hits - 1u;
-    const int i = it * NT + threadIdx.x;
-    const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-    sm.list[base++] = (uint16_t)(ly * TW + lx);
-  }
+  const auto tix = [&](int it) {
+    const int i = it * NT + (int)threadIdx.x;
+    return (uint16_t)((i / Reg<2>::W - 2) * TW + (i % Reg<2>::W - 2));
+  };
+  warp_emit(hits_f, &sm.nlist2, sm.list, -1, tix);
+  warp_emit(hits, &sm.nlist, sm.list, Reg<4>::N - 1, tix);
 }
 
 template <class XT>
@@ -638,6 +651,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
 
   for (int i = tid; i < 3 * TH * TWW; i += NT) (&sm.pw[0][0][0])[i] = 0u;
+  if (tid == 0) sm.nfine = 0;
 
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
   bool bad = false;
@@ -721,61 +735,49 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
       sm.M3[i] = sm.M3[Reg<3>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
     }
   }
-  // The working image is no longer read: its storage holds S' and list2.
-  float* SpL = sm.spl();          // S' per S'-list entry
-  uint16_t* list2 = sm.list2();   // fine-structure list
-
-  // S' = S - med5(S) at the S'-list pixels.
+  // Steps 4-5 on the sparse items, one block-wide phase: S' = S - med5(S),
+  // the sig and lo bits, and at fine items with S' > sigclip F = max((med3 -
+  // med7(med3))/N, 0.01) and the objlim test S'/F > objlim.  Fine items (the
+  // costly ones) come first and rounds alternate direction, so the cheap
+  // S'-only items of a second round land on the threads without a fine item.
   if (edge) __syncthreads();
-  const unsigned n = sm.nlist;
-  for (unsigned j = tid; j < n; j += NT) {
-    const int i = sm.list[j];
+  const unsigned n = sm.nlist, n2 = sm.nlist2, total = n + n2;
+  unsigned n_eval = 0;
+  for (unsigned r = 0; r * NT < total; ++r) {
+    const unsigned q = r * NT + ((r & 1) ? (NT - 1 - tid) : tid);
+    if (q >= total) continue;
+    const bool fine = q < n2;
+    const int i = fine ? sm.list[q] : sm.list[Reg<4>::N - 1 - (int)(q - n2)];
     const int ly = i / TW, lx = i % TW;
     const int c = Reg<2>::idx(ly, lx);
     const float* wb = sm.S + c - 2 * Reg<2>::W - 2;
-    const auto ld = [&](int i) { return wb[(i / 5) * Reg<2>::W + i % 5]; };
+    const auto ld5 = [&](int e) { return wb[(e / 5) * Reg<2>::W + e % 5]; };
     float m;
-    med5x5_ld<float>(ld, &m);
+    med5x5_ld<float>(ld5, &m);
     const float sp = __fsub_rn(sm.S[c], m);
-    SpL[j] = sp;
-    const bool sat = (sm.flags[i] & 8) != 0;
+    const bool sat = (sm.flags[i] & 8) != 0;  // never set for fine items
     const uint32_t bit = 1u << (lx & 31);
-    if (!sat && sp > f.sigclip) {
-      sm.flags[i] |= 1;
-      atomicOr(&sm.pw[0][ly][lx >> 5], bit);
-    }
     if (!sat && sp > f.lo) atomicOr(&sm.pw[1][ly][lx >> 5], bit);
-  }
-  __syncthreads();
-
-  // Step 5 where S' > sigclip (not saturated): F = max((med3 - med7(med3))/N,
-  // 0.01) and the objlim test S'/F > objlim, from a compacted list.
-  for (unsigned b = 0; b < n; b += NT) {
-    const unsigned j = b + tid;
-    const bool p = j < n && (sm.flags[sm.list[j]] & 1);
-    list_append(p, (uint16_t)j, list2, &sm.nlist2);
-  }
-  __syncthreads();
-  const unsigned n2 = sm.nlist2;
-  for (unsigned t = tid; t < n2; t += NT) {
-    const int j = list2[t];
-    const int i = sm.list[j];
-    const int ly = i / TW, lx = i % TW;
+    if (!fine || !(sp > f.sigclip)) continue;  // S'-only items have S' <= S <= sigclip
+    atomicOr(&sm.pw[0][ly][lx >> 5], bit);
     const int c3 = Reg<3>::idx(ly, lx);
-    const XT* wb = sm.M3 + c3 - 3 * Reg<3>::W - 3;
-    const auto ld = [&](int i) { return KT::key(wb[(i / 7) * Reg<3>::W + i % 7]); };
+    const XT* w7 = sm.M3 + c3 - 3 * Reg<3>::W - 3;
+    const auto ld7 = [&](int e) { return KT::key(w7[(e / 7) * Reg<3>::W + e % 7]); };
     K m7;
-    med7x7_ld<K>(ld, &m7);
+    med7x7_ld<K>(ld7, &m7);
+    ++n_eval;
     const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
-      N = sm.N2[Reg<2>::idx(ly, lx)];
+      N = sm.N2[c];
     else
       N = sm.N[i];
     float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
     F = F < 0.01f ? 0.01f : F;
-    if (__fdiv_rn(SpL[j], F) > f.objlim) atomicOr(&sm.pw[2][ly][lx >> 5], 1u << (lx & 31));
+    if (__fdiv_rn(sp, F) > f.objlim) atomicOr(&sm.pw[2][ly][lx >> 5], bit);
   }
+  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
+  if ((tid & 31) == 0 && n_eval) atomicAdd(&sm.nfine, n_eval);
   __syncthreads();
 
   // Bit-planes of the tile out (only in-frame pixels ever set a bit).
@@ -788,8 +790,8 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     }
   }
   if (tid == 0) {
-    if (n) atomicAdd(&f.st->n_sprime, (unsigned long long)n);
-    if (n2) atomicAdd(&f.st->n_fine, (unsigned long long)n2);
+    if (total) atomicAdd(&f.st->n_sprime, (unsigned long long)total);
+    if (sm.nfine) atomicAdd(&f.st->n_fine, (unsigned long long)sm.nfine);
   }
 }
 
