@@ -2,13 +2,14 @@
 //
 // A context owns a fixed set of slots.  A submitted request (one frame or a
 // batch) takes a free slot, whose device scratch -- per-frame descriptors,
-// per-frame state, two bit-packed mask buffers and three bit-planes per
-// frame, and the tile-queue heads -- is allocated stream-ordered and charged
-// against the context's HBM budget.  The request's work is queued on the
-// caller's stream:
-//   memcpy(descriptors) ; memset(state, heads, M_0) ;
-//   { core_kernel(k) ; grow_kernel(k) } for k = 1..max niter ;
+// per-frame state, two bit-packed mask buffers, three bit-planes and the
+// N table per frame, and the tile-queue heads -- is allocated stream-ordered
+// and charged against the context's HBM budget.  The request's work is
+// queued on the caller's stream:
+//   memcpy(descriptors) ; memset(state, heads, M_0) ; ntab_kernel ;
+//   { core_kernel<u16>(k) ; core_kernel<f32>(k) ; grow_kernel(k) } for k = 1..max niter ;
 //   finalize_kernel ;
+// (each core kernel only where the request has frames of its dtype).
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
 // Iteration control is on the device: an iteration whose predecessor
@@ -32,10 +33,10 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kNtabBytes = 65536 * sizeof(float);  // N per uint16 med5 value
-// Tile-queue heads: one per (kernel, level) plus the final replace.
+// Tile-queue heads: one per (core kernel dtype, level) plus the final replace.
 constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
-constexpr int kHeadCore = 0;
-constexpr int kHeadFinal = kHeadLevels, kHeads = kHeadLevels + 1;
+constexpr int kHeadCore = 0;  // + dtype * kHeadLevels + level
+constexpr int kHeadFinal = 2 * kHeadLevels, kHeads = kHeadFinal + 1;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 struct FrameReq {
@@ -113,17 +114,21 @@ struct lacos_ctx {
   unsigned long long next_ticket = 1;
   std::atomic<int> last_cuda{0};
   int num_sms = 0;
-  int core_variant = 3;                 // index into kCoreVariants
-  int blocks_per_sm_core_v[4] = {1, 1, 1, 1};
+  int core_variant = 3;                 // index into kCoreVariants[dtype]
+  int blocks_per_sm_core_v[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};
   int blocks_per_sm_core = 1;
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
 };
 
-using CoreFn = void (*)(const FrameDesc*, int, unsigned, int, unsigned*);
-// Core-kernel variants: register allocation bounded for 1, 2, 3 or 4 CTAs/SM.
-static const CoreFn kCoreVariants[4] = {core_kernel<1>, core_kernel<2>, core_kernel<3>, core_kernel<4>};
+using CoreFn = void (*)(const FrameDesc*, int, unsigned, unsigned, int, unsigned*);
+// Core-kernel variants by frame dtype (LACOS_F32, LACOS_U16): register
+// allocation bounded for 1, 2, 3 or 4 CTAs/SM.
+static const CoreFn kCoreVariants[2][4] = {
+    {core_kernel<1, float>, core_kernel<2, float>, core_kernel<3, float>, core_kernel<4, float>},
+    {core_kernel<1, uint16_t>, core_kernel<2, uint16_t>, core_kernel<3, uint16_t>, core_kernel<4, uint16_t>}};
+static const size_t kCoreSmem[2] = {kCoreSmemBytes<float>, kCoreSmemBytes<uint16_t>};
 
 static int cuda_fail(lacos_ctx* c, cudaError_t e) {
   if (c) c->last_cuda = (int)e;
@@ -182,9 +187,19 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   unsigned long long total_words = 0;
   unsigned total_gblk = 0;
   int max_niter = 0;
-  for (size_t i = 0; i < fr.size(); ++i) {
+  // Descriptor order: uint16 frames first, so that each dtype's tiles form
+  // one contiguous item range for its core kernel.  Each descriptor keeps
+  // its frame's own state and scratch (request order).
+  std::vector<size_t> order;
+  order.reserve(fr.size());
+  for (int dt : {1, 0})
+    for (size_t i = 0; i < fr.size(); ++i)
+      if (fr[i].dtype == dt) order.push_back(i);
+  unsigned tiles_u16 = 0;
+  for (size_t j = 0; j < fr.size(); ++j) {
+    const size_t i = order[j];
     const FrameReq& f = fr[i];
-    FrameDesc& h = hdesc[i];
+    FrameDesc& h = hdesc[j];
     std::memset(&h, 0, sizeof(h));
     h.x0 = f.frame;
     h.dtype = f.dtype;
@@ -218,6 +233,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.tile_begin = total;
     total += tiles;
     h.tile_end = total;
+    if (f.dtype == LACOS_U16) tiles_u16 = total;
     h.word_begin = total_words;
     total_words += (unsigned long long)f.ny * h.wpr;
     h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
@@ -232,7 +248,12 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     CK(cudaMemsetAsync(d + L.mask_off[i], 0, maskbuf_bytes(fr[i].ny, fr[i].nx), s));
   const int nf = (int)fr.size();
   const int cv = c->core_variant;
-  const unsigned gd = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_core_v[cv]));
+  // Core launches: [dtype] -> item range and grid.
+  const unsigned rng[2][2] = {{tiles_u16, total}, {0, tiles_u16}};
+  unsigned gdt[2];
+  for (int dt = 0; dt < 2; ++dt)
+    gdt[dt] = std::min<unsigned>(rng[dt][1] - rng[dt][0],
+                                 (unsigned)(c->num_sms * c->blocks_per_sm_core_v[dt][cv]));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
   // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
   // [2n+1] after finalize.
@@ -252,8 +273,12 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   ntab_kernel<<<dim3(256, nf), 256, 0, s>>>(ddesc, nf);
   CK(cudaGetLastError());
   for (int k = 1; k <= max_niter; ++k) {
-    kCoreVariants[cv]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, nf, total, k, heads + kHeadCore + k);
-    CK(cudaGetLastError());
+    for (int dt : {1, 0}) {
+      if (!gdt[dt]) continue;
+      kCoreVariants[dt][cv]<<<gdt[dt], NT, kCoreSmem[dt], s>>>(ddesc, nf, rng[dt][0], rng[dt][1], k,
+                                                                heads + kHeadCore + dt * kHeadLevels + k);
+      CK(cudaGetLastError());
+    }
     if (int rc = mark(2 * k - 1)) return rc;
     grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, nf, total_gblk, k);
     CK(cudaGetLastError());
@@ -412,14 +437,15 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   c->slots.resize(max_slots ? max_slots : 64);
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
-    e = cudaFuncSetAttribute(kCoreVariants[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kCoreSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[v], kCoreVariants[v],
-                                                        NT, kCoreSmemBytes);
-    c->blocks_per_sm_core_v[v] = std::max(1, c->blocks_per_sm_core_v[v]);
-  }
+  for (int dt = 0; dt < 2; ++dt)
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+      e = cudaFuncSetAttribute(kCoreVariants[dt][v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kCoreSmem[dt]);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[dt][v], kCoreVariants[dt][v],
+                                                          NT, kCoreSmem[dt]);
+      c->blocks_per_sm_core_v[dt][v] = std::max(1, c->blocks_per_sm_core_v[dt][v]);
+    }
   if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
     const int v = std::atoi(env);
     if (v >= 0 && v < 4) c->core_variant = v;
@@ -590,7 +616,7 @@ __device__ __align__(256) unsigned char g_static_scratch[LACOS_STATIC_SCRATCH_BY
 struct StaticDevice {
   bool ready = false;
   void* scratch = nullptr;  // device address of g_static_scratch on this device
-  int num_sms = 0, bpsm_core = 1, bpsm_final = 1, core_variant = 3;
+  int num_sms = 0, bpsm_core[2] = {1, 1}, bpsm_final = 1, core_variant = 3;
 };
 std::mutex g_static_mu;
 constexpr int kStaticMaxDevices = 64;
@@ -612,16 +638,17 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
       if (v >= 0 && v < 4) sd.core_variant = v;
     }
     e = cudaDeviceGetAttribute(&sd.num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kCoreVariants[sd.core_variant],
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core, kCoreVariants[sd.core_variant],
-                                                        NT, kCoreSmemBytes);
+    for (int dt = 0; dt < 2 && e == cudaSuccess; ++dt) {
+      e = cudaFuncSetAttribute(kCoreVariants[dt][sd.core_variant],
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmem[dt]);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core[dt], kCoreVariants[dt][sd.core_variant],
+                                                          NT, kCoreSmem[dt]);
+      sd.bpsm_core[dt] = std::max(1, sd.bpsm_core[dt]);
+    }
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, NT, 0);
     if (e != cudaSuccess) return e;
-    sd.bpsm_core = std::max(1, sd.bpsm_core);
     sd.bpsm_final = std::max(1, sd.bpsm_final);
     sd.ready = true;
   }
@@ -701,12 +728,13 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
       cudaMemsetAsync(dstate, 0, sizeof(FrameState), s) != cudaSuccess ||
       cudaMemsetAsync(h.mbuf0, 0, mb, s) != cudaSuccess)
     return LACOS_ECUDA;
-  const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core));
+  const int di = f.dtype == LACOS_U16 ? 1 : 0;
+  const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core[di]));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   for (int k = 1; k <= p->niter; ++k) {
-    kCoreVariants[sd->core_variant]<<<gd, NT, kCoreSmemBytes, s>>>(ddesc, 1, total, k,
-                                                                       heads + kHeadCore + k);
+    kCoreVariants[di][sd->core_variant]<<<gd, NT, kCoreSmem[di], s>>>(ddesc, 1, 0, total, k,
+                                                                      heads + kHeadCore + di * kHeadLevels + k);
     grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, 1, total_gblk, k);
   }
   finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, 1, total, heads + kHeadFinal);

@@ -29,6 +29,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <type_traits>
@@ -431,8 +432,19 @@ template <> struct CoreSmemT<uint16_t> {
   unsigned nfine;
 };
 static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list array");
-constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<float>) > sizeof(CoreSmemT<uint16_t>)
-                                      ? sizeof(CoreSmemT<float>) : sizeof(CoreSmemT<uint16_t>);
+// Alignment of the vector accesses: 16-byte staging rows (X; Mb in 8-byte
+// groups), 4-pixel block-network loads, 2-pixel pairs of S, N/N2 and flags.
+template <class T>
+constexpr bool core_layout_ok() {
+  return offsetof(T, X) % 16 == 0 && offsetof(T, Mb) % 8 == 0 && offsetof(T, S) % 8 == 0 &&
+         offsetof(T, flags) % 2 == 0;
+}
+static_assert(core_layout_ok<CoreSmemT<float>>() && core_layout_ok<CoreSmemT<uint16_t>>(), "core layout");
+static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, N2) % 8 == 0,
+              "core layout");
+// Dynamic shared memory of a core launch, by working-image type.
+template <class XT>
+constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<XT>);
 
 __device__ __forceinline__ U16x2 pack2(uint16_t lo, uint16_t hi) {
   return U16x2{(uint32_t)lo | ((uint32_t)hi << 16)};
@@ -598,41 +610,69 @@ __device__ __forceinline__ void warp_emit(uint32_t hits, unsigned* cnt, uint16_t
 template <class XT>
 __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& sm, int oy, int ox) {
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
-  constexpr int IT = (Reg<2>::N + NT - 1) / NT;
-  static_assert(IT <= 32, "one bit per iteration");
-  uint32_t hits = 0, hits_f = 0;  // bit it: the pixel of iteration it is an S'-only / fine item
+  // Horizontal pixel pairs (even columns): 2-pixel aligned shared accesses.
+  constexpr int PW = Reg<2>::W / 2;       // pairs per R2 row
+  constexpr int NP = PW * Reg<2>::Hh;     // pairs on R2
+  constexpr int IT = (NP + NT - 1) / NT;  // pairs per thread
+  static_assert(Reg<2>::W % 2 == 0 && XR6::W % 2 == 0 && TW % 2 == 0 && 2 * IT <= 32, "pairs");
+  uint32_t hits = 0, hits_f = 0;  // bit 2*it+e: pixel e of pair it is an S'-only / fine item
+#pragma unroll 1
   for (int it = 0; it < IT; ++it) {
-    const int i = it * NT + threadIdx.x;
-    if (i < Reg<2>::N) {
-      const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
-      const int c = XR6::idx(ly, lx);
-      float L, N;
-      if constexpr (kU16) {
-        L = lplus_int(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
-        N = sm.N2[i];
-      } else {
-        L = lplus(sm.X[c], sm.X[c - XR6::W], sm.X[c + XR6::W], sm.X[c - 1], sm.X[c + 1]);
-        N = noise_of(f, sm.S[i]);
-      }
-      const float S = __fdiv_rn(L, __fadd_rn(N, N));
-      sm.S[i] = S;
-      if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
-        const int t = ly * TW + lx;
-        if constexpr (!kU16) sm.N[t] = N;
-        const bool sat = f.satlevel > 0.0f && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
-        sm.flags[t] = sat ? 8 : 0;
-        if ((oy + ly) < f.ny && (ox + lx) < f.nx) {
-          if (!sat && S > f.sigclip)
-            hits_f |= 1u << it;
-          else if (S > f.thr_min)
-            hits |= 1u << it;
+    const int q = it * NT + (int)threadIdx.x;
+    if (q >= NP) break;
+    const int ly = q / PW - 2, lx = (q % PW) * 2 - 2;
+    const int c = XR6::idx(ly, lx), i2 = Reg<2>::idx(ly, lx);
+    float L0, L1, N0, N1;
+    if constexpr (kU16) {
+      const auto ld2 = [&](int o) { return *reinterpret_cast<const uint32_t*>(sm.X + o); };
+      const uint32_t mid = ld2(c), lft = ld2(c - 2), rgt = ld2(c + 2);
+      const uint32_t up = ld2(c - XR6::W), dn = ld2(c + XR6::W);
+      const int v0 = (int)(mid & 0xffffu), v1 = (int)(mid >> 16);
+      L0 = lplus_int(v0, (int)(up & 0xffffu), (int)(dn & 0xffffu), (int)(lft >> 16), v1);
+      L1 = lplus_int(v1, (int)(up >> 16), (int)(dn >> 16), v0, (int)(rgt & 0xffffu));
+      const float2 nn = *reinterpret_cast<const float2*>(sm.N2 + i2);
+      N0 = nn.x;
+      N1 = nn.y;
+    } else {
+      const auto ld2 = [&](int o) { return *reinterpret_cast<const float2*>(sm.X + o); };
+      const float2 mid = ld2(c), lft = ld2(c - 2), rgt = ld2(c + 2);
+      const float2 up = ld2(c - XR6::W), dn = ld2(c + XR6::W);
+      L0 = lplus(mid.x, up.x, dn.x, lft.y, mid.y);
+      L1 = lplus(mid.y, up.y, dn.y, mid.x, rgt.x);
+      const float2 m = *reinterpret_cast<const float2*>(sm.S + i2);
+      N0 = noise_of(f, m.x);
+      N1 = noise_of(f, m.y);
+    }
+    const float S0 = __fdiv_rn(L0, __fadd_rn(N0, N0));
+    const float S1 = __fdiv_rn(L1, __fadd_rn(N1, N1));
+    *reinterpret_cast<float2*>(sm.S + i2) = make_float2(S0, S1);
+    if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
+      const int t = ly * TW + lx;
+      if constexpr (!kU16) *reinterpret_cast<float2*>(sm.N + t) = make_float2(N0, N1);
+      const bool chk = f.satlevel > 0.0f;
+      const bool sat0 = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
+      const bool sat1 = chk && !sm.Mb[c + 1] && (float)sm.X[c + 1] >= f.satlevel;
+      *reinterpret_cast<uint16_t*>(sm.flags + t) = (uint16_t)((sat0 ? 8 : 0) | (sat1 ? 0x800 : 0));
+      if ((oy + ly) < f.ny) {
+        const uint32_t b0 = 1u << (2 * it), b1 = b0 << 1;
+        if ((ox + lx) < f.nx) {
+          if (!sat0 && S0 > f.sigclip)
+            hits_f |= b0;
+          else if (S0 > f.thr_min)
+            hits |= b0;
+        }
+        if ((ox + lx + 1) < f.nx) {
+          if (!sat1 && S1 > f.sigclip)
+            hits_f |= b1;
+          else if (S1 > f.thr_min)
+            hits |= b1;
         }
       }
     }
   }
-  const auto tix = [&](int it) {
-    const int i = it * NT + (int)threadIdx.x;
-    return (uint16_t)((i / Reg<2>::W - 2) * TW + (i % Reg<2>::W - 2));
+  const auto tix = [&](int bit) {
+    const int q = (bit >> 1) * NT + (int)threadIdx.x;
+    return (uint16_t)((q / PW - 2) * TW + (q % PW) * 2 - 2 + (bit & 1));
   };
   warp_emit(hits_f, &sm.nlist2, sm.list, -1, tix);
   warp_emit(hits, &sm.nlist, sm.list, Reg<4>::N - 1, tix);
@@ -796,25 +836,26 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
 }
 
 // MINB: resident CTAs per SM the register allocation is bounded for (the
-// variants trade registers, and so spills, against occupancy).  Each tile
-// takes the path of its frame's dtype.
-template <int MINB>
+// variants trade registers, and so spills, against occupancy).  One kernel
+// per working-image type: a request orders its frames so that each type's
+// tiles form one contiguous item range [item_begin, item_end), and a launch
+// walks only its own range (its own queue head).
+template <int MINB, class XT>
 __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                        unsigned total, int k, unsigned* head) {
+                                                        unsigned item_begin, unsigned item_end, int k,
+                                                        unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_item;
+  constexpr int kDtype = std::is_same<XT, uint16_t>::value ? 1 : 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(head, 1u);
+    if (threadIdx.x == 0) s_item = item_begin + atomicAdd(head, 1u);
     __syncthreads();
     const unsigned item = s_item;
     __syncthreads();
-    if (item >= total) break;
+    if (item >= item_end) break;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    if (!iteration_runs(f, k)) continue;
-    if (f.dtype == 1)
-      core_tile<uint16_t>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<uint16_t>*>(smem_raw));
-    else
-      core_tile<float>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<float>*>(smem_raw));
+    if (f.dtype != kDtype || !iteration_runs(f, k)) continue;
+    core_tile<XT>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<XT>*>(smem_raw));
     __syncthreads();
   }
 }
