@@ -888,10 +888,15 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
 // 2-row, 2-word halo) and the first growth g1 = dil3(cand) & sig (1-row,
 // 1-word halo) are staged in shared memory; each thread then forms
 // g2 = dil3(g1) & lo for its word, M_k = M_{k-1} | g2, and counts new flags.
+// Every global load of the block (candidate, sig, lo and mask words) is
+// issued up front, so the block waits for one memory round trip.
 __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                   unsigned total_blocks, int k) {
-  __shared__ uint32_t C[GB_H + 4][GB_W + 4];
-  __shared__ uint32_t G1[GB_H + 2][GB_W + 2];
+  constexpr int CW = GB_W + 4, CN = (GB_H + 4) * CW;  // candidate region
+  constexpr int GW = GB_W + 2, GN = (GB_H + 2) * GW;  // g1 region
+  constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
+  __shared__ uint32_t C[GB_H + 4][CW];
+  __shared__ uint32_t G1[GB_H + 2][GW];
   __shared__ unsigned s_cnt;
   const int tid = threadIdx.x;
   const unsigned blk = blockIdx.x;
@@ -901,31 +906,49 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
   const unsigned b = blk - f.gblk_begin;
   const int y0 = (int)(b / (unsigned)f.gblk_x) * GB_H, w0 = (int)(b % (unsigned)f.gblk_x) * GB_W;
   const int ny = f.ny, wpr = f.wpr;
-  if (tid == 0) s_cnt = 0;
-  for (int i = tid; i < (GB_H + 4) * (GB_W + 4); i += NT) {
-    const int r = i / (GB_W + 4), c = i % (GB_W + 4);
-    C[r][c] = plane_word(f.p_cand, ny, wpr, y0 - 2 + r, w0 - 2 + c);
-  }
-  __syncthreads();
-  for (int i = tid; i < (GB_H + 2) * (GB_W + 2); i += NT) {
-    const int r = i / (GB_W + 2), c = i % (GB_W + 2);
-    uint32_t d = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][c], C[r + a][c + 1], C[r + a][c + 2]);
-    G1[r][c] = d & plane_word(f.p_sig, ny, wpr, y0 - 1 + r, w0 - 1 + c);
-  }
-  __syncthreads();
   const int ty = tid / GB_W, tx = tid % GB_W;
   const int y = y0 + ty, w = w0 + tx;
+  const bool own = y < ny && w < wpr;
+  const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
+  uint32_t cw[CP], sw[GP];
+#pragma unroll
+  for (int p = 0; p < CP; ++p) {
+    const int i = p * NT + tid;
+    cw[p] = i < CN ? plane_word(f.p_cand, ny, wpr, y0 - 2 + i / CW, w0 - 2 + i % CW) : 0u;
+  }
+#pragma unroll
+  for (int p = 0; p < GP; ++p) {
+    const int i = p * NT + tid;
+    sw[p] = i < GN ? plane_word(f.p_sig, ny, wpr, y0 - 1 + i / GW, w0 - 1 + i % GW) : 0u;
+  }
+  const uint32_t lo = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
+  const uint32_t mp = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
+  if (tid == 0) s_cnt = 0;
+#pragma unroll
+  for (int p = 0; p < CP; ++p) {
+    const int i = p * NT + tid;
+    if (i < CN) C[i / CW][i % CW] = cw[p];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < GP; ++p) {
+    const int i = p * NT + tid;
+    if (i < GN) {
+      const int r = i / GW, c = i % GW;
+      uint32_t d = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][c], C[r + a][c + 1], C[r + a][c + 2]);
+      G1[r][c] = d & sw[p];
+    }
+  }
+  __syncthreads();
   unsigned cnt = 0;
-  if (y < ny && w < wpr) {
+  if (own) {
     uint32_t d2 = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) d2 |= hdil(G1[ty + a][tx], G1[ty + a][tx + 1], G1[ty + a][tx + 2]);
-    const uint32_t g2 = d2 & plane_word(f.p_lo, ny, wpr, y, w);
-    const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
+    const uint32_t g2 = d2 & lo;
     uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
-    const uint32_t mp = __ldg(Mp + (size_t)y * wpr + w);
     Mn[(size_t)y * wpr + w] = mp | g2;
     cnt = __popc(g2 & ~mp);
   }
