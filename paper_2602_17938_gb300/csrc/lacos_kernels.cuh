@@ -437,7 +437,7 @@ static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list
 template <class T>
 constexpr bool core_layout_ok() {
   return offsetof(T, X) % 16 == 0 && offsetof(T, Mb) % 8 == 0 && offsetof(T, S) % 8 == 0 &&
-         offsetof(T, flags) % 2 == 0;
+         offsetof(T, flags) % 4 == 0;
 }
 static_assert(core_layout_ok<CoreSmemT<float>>() && core_layout_ok<CoreSmemT<uint16_t>>(), "core layout");
 static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, N2) % 8 == 0,
@@ -487,20 +487,78 @@ struct QuadLoaderU16 {
   }
 };
 
+// Assignment of the dense step's block units to (round, thread): the med5
+// units first, the med3 units after them starting at a warp boundary, so
+// that no warp runs both kinds (a warp with both would execute the two
+// networks one after the other).
+template <int S_UNITS, int M_UNITS>
+struct UnitMap {
+  static constexpr int RS = (S_UNITS + NT - 1) / NT;     // rounds with med5 units
+  static constexpr int REM = S_UNITS - (RS - 1) * NT;    // med5 units in the last of them
+  static constexpr int MF = (REM + 31) / 32 * 32;        // its first med3 thread
+  static constexpr int M0 = NT - MF;                     // med3 units that round can take
+  static constexpr int ROUNDS = RS + (M_UNITS > M0 ? (M_UNITS - M0 + NT - 1) / NT : 0);
+  // Unit of thread t in round r (< S_UNITS: med5, else med3), or -1.
+  __device__ static __forceinline__ int unit(int r, int t) {
+    if (r < RS - 1) return r * NT + t;
+    if (r == RS - 1) {
+      if (t < REM) return r * NT + t;
+      return (t >= MF && t - MF < M_UNITS) ? S_UNITS + (t - MF) : -1;
+    }
+    const int m = M0 + (r - RS) * NT + t;
+    return m < M_UNITS ? S_UNITS + m : -1;
+  }
+};
+
+// Saturation flags of the tile (the original input at an unflagged pixel),
+// four pixels per item, by the threads from FIRST on (for uint16 frames the
+// block threads without a med5 block, which would otherwise wait at the next
+// barrier).
+template <class XT, int FIRST, class SM>
+__device__ __forceinline__ void sat_flags(const FrameDesc& f, SM& sm) {
+  static_assert(FIRST >= 0 && FIRST < NT, "some threads must take the flags");
+  constexpr int first = FIRST;
+  const int tid = (int)threadIdx.x;
+  if (tid < first) return;
+  const bool chk = f.satlevel > 0.0f;
+  for (int q = tid - first; q < TH * TW / 4; q += NT - first) {
+    const int ly = q / (TW / 4), lx = (q % (TW / 4)) * 4;
+    const int c = XR6::idx(ly, lx);
+    float v[4];
+    if constexpr (std::is_same<XT, float>::value) {
+      const float4 x = *reinterpret_cast<const float4*>(sm.X + c);
+      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+      const uint2 x = *reinterpret_cast<const uint2*>(sm.X + c);
+      v[0] = (float)(x.x & 0xffffu); v[1] = (float)(x.x >> 16);
+      v[2] = (float)(x.y & 0xffffu); v[3] = (float)(x.y >> 16);
+    }
+    const uint32_t mb = *reinterpret_cast<const uint32_t*>(sm.Mb + c);
+    uint32_t fl = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (chk && !((mb >> (8 * e)) & 0xffu) && v[e] >= f.satlevel) fl |= 8u << (8 * e);
+    *reinterpret_cast<uint32_t*>(sm.flags + ly * TW + lx) = fl;
+  }
+}
+
 // Dense networks for float32 frames: med5 on R2 by 4x2 blocks (parked in
 // S), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
 // positions (from clamped inputs); those are overwritten by the edge fill.
 __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& sm) {
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
   constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
-  constexpr int S_UNITS = S_UX * S_UY, ALL_UNITS = S_UNITS + M_UX * M_UY;
+  constexpr int S_UNITS = S_UX * S_UY;
+  using UM = UnitMap<S_UNITS, M_UX * M_UY>;
   static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && (TH + 6) % M_BH == 0, "block tiling");
   // Window columns start at lx0 - 2 = 4u - 4 (med5) and lx0 - 1 = 8m - 4
   // (med3): 4-pixel aligned in the 8-column-halo staging rows; the med3
   // window's last 4-group reads at most 2 pixels past it, still in the row.
   static_assert(XR6::W % 4 == 0 && XR6::idx(0, -4) % 4 == 0 && (-3 + 8 * (M_UX - 1)) - 1 + 12 <= TW + 8,
                 "aligned block windows");
-  for (int u = threadIdx.x; u < ALL_UNITS; u += NT) {
+  for (int rd = 0; rd < UM::ROUNDS; ++rd) {
+    const int u = UM::unit(rd, threadIdx.x);
+    if (u < 0) continue;
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
@@ -526,6 +584,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
           if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
     }
   }
+  sat_flags<float, 0>(f, sm);  // units outnumber threads here: all threads share the flags
 }
 
 // Dense part for uint16 frames: the same blocks on packed uint16 pairs, two
@@ -538,9 +597,13 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
   constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
   constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW;
   constexpr int M_PAIRS = ((TH + 6) / M_BH + 1) / 2, M_DY = M_PAIRS * M_BH;
-  constexpr int S_UNITS = S_UX * S_PAIRS, ALL_UNITS = S_UNITS + M_UX * M_PAIRS;
+  constexpr int S_UNITS = S_UX * S_PAIRS;
+  using UM = UnitMap<S_UNITS, M_UX * M_PAIRS>;
   static_assert(((TH + 4) / S_BH) % 2 == 0, "S row-pairs pair up");
-  for (int u = threadIdx.x; u < ALL_UNITS; u += NT) {
+  static_assert(UM::ROUNDS == 1, "one unit per thread");
+  for (int rd = 0; rd < UM::ROUNDS; ++rd) {
+    const int u = UM::unit(rd, threadIdx.x);
+    if (u < 0) continue;
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
@@ -573,6 +636,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
         }
     }
   }
+  sat_flags<uint16_t, UM::MF>(f, sm);  // the med3 warps
 }
 
 // Appends val(it) for every set bit `it` of each lane's `hits` to a shared
@@ -649,10 +713,8 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
     if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
       const int t = ly * TW + lx;
       if constexpr (!kU16) *reinterpret_cast<float2*>(sm.N + t) = make_float2(N0, N1);
-      const bool chk = f.satlevel > 0.0f;
-      const bool sat0 = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
-      const bool sat1 = chk && !sm.Mb[c + 1] && (float)sm.X[c + 1] >= f.satlevel;
-      *reinterpret_cast<uint16_t*>(sm.flags + t) = (uint16_t)((sat0 ? 8 : 0) | (sat1 ? 0x800 : 0));
+      const uint32_t fl = *reinterpret_cast<const uint16_t*>(sm.flags + t);  // from sat_flags
+      const bool sat0 = (fl & 8u) != 0, sat1 = (fl & 0x800u) != 0;
       if ((oy + ly) < f.ny) {
         const uint32_t b0 = 1u << (2 * it), b1 = b0 << 1;
         if ((ox + lx) < f.nx) {
