@@ -26,8 +26,8 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (5 bits per pixel plus 256 KiB per frame),
- * charged against the context's HBM budget.
+ * its scratch (5 bits per pixel, plus 256 KiB and 3 bytes per 32x64 tile
+ * per frame), charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
  * are the LACOS_E* codes below; lacos_poll also returns LACOS_PENDING (1).
@@ -143,6 +143,8 @@ typedef struct {
   long long n_fine;                    /* pixels where the fine-structure F was evaluated */
   long long n_replace;                 /* masked-median replacements inside core launches */
   long long n_replace_wide;            /* ... of which the 5x5 window was fully flagged */
+  long long px_core;                   /* tile pixels the core kernel computed, all levels (a
+                                          level recomputes only tiles whose inputs changed) */
 } lacos_profile;
 
 int lacos_set_profiling(lacos_ctx *c, int on);

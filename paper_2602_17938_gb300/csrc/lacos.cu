@@ -81,6 +81,10 @@ bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) 
 
 int wpr_of(int nx) { return (nx + 31) / 32; }
 size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
+// Per-tile level marks of the core kernel: two ping-pong bytes and a sticky one per tile.
+size_t tflag_bytes(int ny, int nx) {
+  return align_up(3 * (size_t)((nx + TW - 1) / TW) * (size_t)((ny + TH - 1) / TH));
+}
 
 struct Layout {
   size_t heads, descs, states, masks, total;
@@ -97,7 +101,7 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 5 * maskbuf_bytes(f.ny, f.nx) + kNtabBytes;  // M 0/1, sig/lo/cand, N table
+    off += 5 * maskbuf_bytes(f.ny, f.nx) + kNtabBytes + tflag_bytes(f.ny, f.nx);  // M 0/1, sig/lo/cand, N table, tile marks
   }
   L.total = off;
   return L;
@@ -213,6 +217,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
     h.ntab = (float*)(d + L.mask_off[i] + 5 * mb);
+    h.tflags = (uint8_t*)(d + L.mask_off[i] + 5 * mb + kNtabBytes);
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -244,8 +249,11 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(heads, 0, sizeof(unsigned) * kHeads, s));
   CK(cudaMemsetAsync(dstate, 0, sizeof(FrameState) * fr.size(), s));
-  for (size_t i = 0; i < fr.size(); ++i)
-    CK(cudaMemsetAsync(d + L.mask_off[i], 0, maskbuf_bytes(fr[i].ny, fr[i].nx), s));
+  for (size_t i = 0; i < fr.size(); ++i) {
+    const size_t mb = maskbuf_bytes(fr[i].ny, fr[i].nx);
+    CK(cudaMemsetAsync(d + L.mask_off[i], 0, mb, s));  // M_0
+    CK(cudaMemsetAsync(d + L.mask_off[i] + 5 * mb + kNtabBytes, 0, tflag_bytes(fr[i].ny, fr[i].nx), s));
+  }
   const int nf = (int)fr.size();
   const int cv = c->core_variant;
   // Core launches: [dtype] -> item range and grid.
@@ -399,6 +407,7 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
       P.n_fine += (long long)hs[i].n_fine;
       P.n_replace += (long long)hs[i].n_replace;
       P.n_replace_wide += (long long)hs[i].n_replace_wide;
+      P.px_core += (long long)hs[i].px_core;
     }
   }
   for (int i = 0; i < sl.nframes; ++i) {
@@ -670,7 +679,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const size_t off_desc = align_up(sizeof(unsigned) * kHeads);
   const size_t off_state = off_desc + align_up(sizeof(FrameDesc));
   const size_t off_masks = off_state + align_up(sizeof(FrameState));
-  const size_t need = off_masks + 5 * mb + kNtabBytes;
+  const size_t need = off_masks + 5 * mb + kNtabBytes + tflag_bytes(ny, nx);
   if (need > (size_t)LACOS_STATIC_SCRATCH_BYTES) return LACOS_ENOMEM;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LACOS_ECUDA;
@@ -696,6 +705,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.p_lo = (uint32_t*)(planes + 3 * mb);
   h.p_cand = (uint32_t*)(planes + 4 * mb);
   h.ntab = (float*)(planes + 5 * mb);
+  h.tflags = (uint8_t*)(planes + 5 * mb + kNtabBytes);
   h.mask_out = d_mask;
   h.clean_out = d_clean;
   h.st = dstate;
@@ -726,7 +736,8 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;
   if (cudaMemsetAsync(heads, 0, sizeof(unsigned) * kHeads, s) != cudaSuccess ||
       cudaMemsetAsync(dstate, 0, sizeof(FrameState), s) != cudaSuccess ||
-      cudaMemsetAsync(h.mbuf0, 0, mb, s) != cudaSuccess)
+      cudaMemsetAsync(h.mbuf0, 0, mb, s) != cudaSuccess ||
+      cudaMemsetAsync(h.tflags, 0, tflag_bytes(ny, nx), s) != cudaSuccess)
     return LACOS_ECUDA;
   const int di = f.dtype == LACOS_U16 ? 1 : 0;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core[di]));

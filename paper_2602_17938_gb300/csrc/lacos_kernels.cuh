@@ -80,6 +80,7 @@ struct FrameState {
   unsigned long long flagged;                      // pixels in the final mask
   unsigned long long n_sprime, n_fine, n_replace;  // sparse-work counters (profiling)
   unsigned long long n_replace_wide;               // replacements whose 5x5 window was all flagged
+  unsigned long long px_core;                      // tile pixels the core kernel computed (all levels)
   unsigned int err;
   int iters_run;
 };
@@ -94,6 +95,7 @@ struct FrameDesc {
   uint32_t* p_lo;
   uint32_t* p_cand;
   float* ntab;       // uint16 frames: N for every integer med5 value 0..65535
+  uint8_t* tflags;   // per core tile: [2][tiles] "recompute at level k" (buffer k & 1), [tiles] sticky
   uint8_t* mask_out;
   float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
@@ -201,6 +203,9 @@ __device__ __forceinline__ bool iteration_runs(const FrameDesc& f, int k) {
   if (k > f.niter) return false;
   return k == 1 || *(volatile unsigned long long*)&f.st->fresh[k - 1] != 0;
 }
+
+// Core tiles of a frame.
+__device__ __forceinline__ unsigned tiles_of(const FrameDesc& f) { return f.tile_end - f.tile_begin; }
 
 // Iteration count actually executed (early stop included).
 __device__ __forceinline__ int run_of(const FrameDesc& f) {
@@ -797,6 +802,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
         const int ly = c / XR6::W - 6, lx = c % XR6::W - 8;
         v = (XT)maskmed_wide(f, Mp, oy + ly, ox + lx, 3);
         atomicAdd(&f.st->n_replace_wide, 1ull);
+        f.tflags[2 * tiles_of(f) + tix] = 1;  // this tile now depends on more than tile + 6
       }
       sm.X[c] = v;
     }
@@ -892,6 +898,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     }
   }
   if (tid == 0) {
+    atomicAdd(&f.st->px_core, (unsigned long long)(min(TH, ny - oy) * min(TW, nx - ox)));
     if (total) atomicAdd(&f.st->n_sprime, (unsigned long long)total);
     if (sm.nfine) atomicAdd(&f.st->n_fine, (unsigned long long)sm.nfine);
   }
@@ -908,18 +915,60 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
                                                         unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_item;
+  __shared__ int s_run;
   constexpr int kDtype = std::is_same<XT, uint16_t>::value ? 1 : 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = item_begin + atomicAdd(head, 1u);
+    if (threadIdx.x == 0) {
+      const unsigned item = item_begin + atomicAdd(head, 1u);
+      int run = 0;
+      if (item < item_end) {
+        const FrameDesc& f = fr[frame_of(fr, nframes, item)];
+        run = f.dtype == kDtype && iteration_runs(f, k);
+        if (run && k > 1) {  // levels after the first: only the tiles whose inputs changed
+          const unsigned t = item - f.tile_begin;
+          uint8_t* mk = f.tflags + (size_t)(k & 1) * tiles_of(f) + t;
+          run = *mk || f.tflags[2 * tiles_of(f) + t];
+          *mk = 0;
+        }
+      }
+      s_item = item;
+      s_run = run;
+    }
     __syncthreads();
     const unsigned item = s_item;
+    const int run = s_run;
     __syncthreads();
     if (item >= item_end) break;
+    if (!run) continue;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    if (f.dtype != kDtype || !iteration_runs(f, k)) continue;
     core_tile<XT>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<XT>*>(smem_raw));
     __syncthreads();
   }
+}
+
+// ---- which core tiles a level must recompute -------------------------------
+//
+// A core tile's bit-planes at level k+1 depend on the mask M_k only within
+// its tile + 6 (the replacement windows of tile + 4 and the saturation flags),
+// unless a replacement there needed a window wider than 5x5.  So a tile with
+// no pixel newly flagged by level k within 6 pixels, and no wide window so
+// far, would recompute exactly the planes it already holds: level k+1 skips
+// it.  grow_kernel(k) marks the tiles near its new flags; core_kernel(k+1)
+// reads and clears the mark; a tile that needs a wide window is marked for
+// good.
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Marks for level kn every tile whose rows/columns +-6 hold a set bit of
+// `bits`, the new flags of word w of row y.
+__device__ __forceinline__ void mark_tiles(const FrameDesc& f, int kn, int y, int w, uint32_t bits) {
+  const int x_lo = w * 32 + __ffs(bits) - 1, x_hi = w * 32 + 31 - __clz(bits);
+  const int tiles_y = (f.ny + TH - 1) / TH;
+  const int ty0 = max(0, floordiv(y - TH - 6, TH) + 1), ty1 = min(tiles_y - 1, (y + 6) / TH);
+  const int tx0 = max(0, floordiv(x_lo - TW - 6, TW) + 1), tx1 = min(f.tiles_x - 1, (x_hi + 6) / TW);
+  uint8_t* d = f.tflags + (size_t)(kn & 1) * tiles_of(f);
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) d[ty * f.tiles_x + tx] = 1;
 }
 
 // ---- step 6: growth on 32-pixel words --------------------------------------
@@ -1012,7 +1061,9 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
     const uint32_t g2 = d2 & lo;
     uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
     Mn[(size_t)y * wpr + w] = mp | g2;
-    cnt = __popc(g2 & ~mp);
+    const uint32_t fresh = g2 & ~mp;
+    cnt = __popc(fresh);
+    if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);

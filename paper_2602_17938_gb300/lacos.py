@@ -43,7 +43,8 @@ class Profile(ctypes.Structure):
                 ("grow_ms", ctypes.c_float * MAX_NITER),
                 ("final_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
                 ("n_sprime", ctypes.c_longlong), ("n_fine", ctypes.c_longlong),
-                ("n_replace", ctypes.c_longlong), ("n_replace_wide", ctypes.c_longlong)]
+                ("n_replace", ctypes.c_longlong), ("n_replace_wide", ctypes.c_longlong),
+                ("px_core", ctypes.c_longlong)]
 
 
 class Result(ctypes.Structure):
@@ -237,7 +238,8 @@ class Context:
         return {"core_ms": list(p.core_ms[:n]), "grow_ms": list(p.grow_ms[:n]),
                 "final_ms": p.final_ms,
                 "px_iterations": p.px_iterations, "n_sprime": p.n_sprime, "n_fine": p.n_fine,
-                "n_replace": p.n_replace, "n_replace_wide": p.n_replace_wide}
+                "n_replace": p.n_replace, "n_replace_wide": p.n_replace_wide,
+                "px_core": p.px_core}
 
     def last_cuda_error(self) -> int:
         return self.lib.lacos_last_cuda_error(self.h)

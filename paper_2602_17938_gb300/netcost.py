@@ -34,9 +34,12 @@ def counts() -> dict:
 
 
 def detect_minmax_ops(profile: dict) -> int:
-    """Min/max operations of all detect launches of one request."""
+    """Min/max operations of all detect launches of one request: the dense
+    networks at the tile pixels the core kernel computed (a level skips the
+    tiles whose inputs did not change) and med5 at each S' evaluation."""
     c = counts()
-    return int(profile["px_iterations"] * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
+    px = profile.get("px_core", profile["px_iterations"])
+    return int(px * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
                + profile["n_sprime"] * c["med5x5"])
 
 
