@@ -214,19 +214,6 @@ __device__ __forceinline__ int run_of(const FrameDesc& f) {
   return f.niter;
 }
 
-// Warp-aggregated append of `val` to a shared list when `pred` holds.  All
-// 32 lanes of the warp must call it.
-__device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* lst, unsigned* cnt) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) lst[base + __popc(m & ((1u << lane) - 1u))] = val;
-}
-
 // Selection keys of the working-image types: float values are their own
 // keys (finite, -0 canonicalised) with -inf/+inf as sentinels; uint16 values
 // become int keys with -1 and 65536 as sentinels.
@@ -1099,11 +1086,15 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
   stage_x0_mask<3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
-  for (int b = 0; b < TH * TW; b += NT) {
-    const int i = b + tid;
-    const int ly = i / TW, lx = i % TW;
-    const bool p = (oy + ly) < f.ny && (ox + lx) < f.nx && sm.Mb[XR3::idx(ly, lx)];
-    list_append(p, (uint16_t)i, sm.list, &sm.nlist);
+  // The tile's flagged pixels straight from the staged mask words (the
+  // tile's columns are whole words; bits beyond the frame are never set):
+  // the first two warps, one word each, one shared atomic per warp.
+  static_assert(TH * TWW % 32 == 0 && TH * TWW <= NT, "whole warps of mask words");
+  if (tid < TH * TWW) {
+    const int ly = tid / TWW, wd = tid % TWW;
+    const int w0 = clampi(ox - 8, 0, f.nx - 1) >> 5;  // as staged
+    const uint32_t bits = (oy + ly) < f.ny ? sm.Mw[ly + 3][((ox >> 5) + wd) - w0] : 0u;
+    warp_emit(bits, &sm.nlist, sm.list, -1, [&](int b) { return (uint16_t)(ly * TW + wd * 32 + b); });
   }
   __syncthreads();
   const unsigned n = sm.nlist;
@@ -1148,7 +1139,7 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
   }
 }
 
-__global__ void __launch_bounds__(NT, 4) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
+__global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                          unsigned total, unsigned* head) {
   __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
   __shared__ unsigned s_item;
