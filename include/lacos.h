@@ -26,7 +26,7 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (5 bits per pixel, plus 256 KiB and 3 bytes per 32x64 tile
+ * its scratch (5 bits per pixel, plus 512 KiB and 3 bytes per 32x64 tile
  * per frame), charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
@@ -158,7 +158,7 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
  * device allocator.  The scratch lives in a fixed array of
  * LACOS_STATIC_SCRATCH_BYTES inside this library's device image, held by
  * every GPU that loads the library until the process exits; frames whose
- * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 107 Mpx,
+ * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 106 Mpx,
  * e.g. 9576 x 6388 fits, 12000 x 12000 does not -- are rejected with
  * LACOS_ENOMEM.  Arguments, layout and results are those of lacos_submit
  * (outputs written to the caller's d_mask and d_clean); the call queues the
@@ -196,6 +196,18 @@ int lacos_last_cuda_error(lacos_ctx *c);
 
 /* Library version string. */
 const char *lacos_version(void);
+
+/* Self-check of the division the uint16 path uses instead of IEEE division
+ * (S = L+/(2N) from a table of 2N and its correctly rounded reciprocal,
+ * with Markstein's correction; the float32 path divides directly).  For the
+ * given gain and read noise it builds the 65536-entry table and compares,
+ * bit for bit, the result with IEEE float32 division for every numerator a
+ * uint16 frame's L+ can take (k/4, k = 0..524280) and every entry: 3.4e10
+ * pairs on the current device, tens of milliseconds.  *mismatches receives
+ * the number of differing pairs (0 means identical everywhere).
+ * Errors: LACOS_EINVAL (null pointer, gain <= 0, negative or non-finite
+ * values), LACOS_ECUDA.  Allocates and frees 8 bytes of device memory. */
+int lacos_selftest_division(float gain, float readnoise, unsigned long long *mismatches);
 
 #ifdef __cplusplus
 }

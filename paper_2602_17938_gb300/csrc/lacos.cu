@@ -32,7 +32,7 @@ using namespace lacos;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kNtabBytes = 65536 * sizeof(float);  // N per uint16 med5 value
+constexpr size_t kNtabBytes = 65536 * sizeof(float2);  // {2N, 1/(2N)} per uint16 med5 value
 // Tile-queue heads: one per (core kernel dtype, level) plus the final replace.
 constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
 constexpr int kHeadCore = 0;  // + dtype * kHeadLevels + level
@@ -216,7 +216,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_sig = (uint32_t*)(d + L.mask_off[i] + 2 * mb);
     h.p_lo = (uint32_t*)(d + L.mask_off[i] + 3 * mb);
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
-    h.ntab = (float*)(d + L.mask_off[i] + 5 * mb);
+    h.ntab = (float2*)(d + L.mask_off[i] + 5 * mb);
     h.tflags = (uint8_t*)(d + L.mask_off[i] + 5 * mb + kNtabBytes);
     h.mask_out = f.mask;
     h.clean_out = f.clean;
@@ -428,6 +428,28 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
 extern "C" {
 
 const char* lacos_version(void) { return "lacos-gb300 0.1 (sm_103a)"; }
+
+int lacos_selftest_division(float gain, float readnoise, unsigned long long* mismatches) {
+  if (!mismatches || !(gain > 0.0f) || !(readnoise >= 0.0f) || !std::isfinite(gain) || !std::isfinite(readnoise))
+    return LACOS_EINVAL;
+  FrameDesc f;
+  std::memset(&f, 0, sizeof(f));
+  f.dtype = LACOS_U16;
+  f.gain = gain;
+  volatile float rn = readnoise;
+  volatile float rn2 = rn * rn;  // as a request forms it
+  f.rn2 = rn2;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) return LACOS_ECUDA;
+  cudaError_t e = cudaMemset(d, 0, sizeof(*d));
+  if (e == cudaSuccess) {
+    selftest_division_kernel<<<65536, 256>>>(f, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(mismatches, d, sizeof(*d), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LACOS_OK : LACOS_ECUDA;
+}
 
 size_t lacos_scratch_bytes(int ny, int nx) {
   if (ny < 1 || nx < 1) return 0;
@@ -704,7 +726,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.p_sig = (uint32_t*)(planes + 2 * mb);
   h.p_lo = (uint32_t*)(planes + 3 * mb);
   h.p_cand = (uint32_t*)(planes + 4 * mb);
-  h.ntab = (float*)(planes + 5 * mb);
+  h.ntab = (float2*)(planes + 5 * mb);
   h.tflags = (uint8_t*)(planes + 5 * mb + kNtabBytes);
   h.mask_out = d_mask;
   h.clean_out = d_clean;

@@ -15,8 +15,10 @@
 //     pixels) and the candidates;
 //   grow_kernel: step 6 on 32-pixel words, M_k = M_{k-1} | g2 and the count
 //     of newly flagged pixels.
-// For uint16 frames N is read from a 65536-entry table of N(med5) built once
-// per request (ntab_kernel), and the dense networks run on packed pairs.
+// For uint16 frames 2N and 1/(2N) are read from a 65536-entry table indexed by
+// med5, built once per request (ntab_kernel), S = L+/(2N) is formed from the
+// reciprocal with two Markstein corrections (div_recip), and the dense
+// networks run on packed pairs.
 // finalize_kernel writes the cleaned frame R(X0, M) and the uint8 mask.
 //
 // Every stage evaluates its own array at in-frame positions only and reads
@@ -94,7 +96,7 @@ struct FrameDesc {
   uint32_t* p_sig;   // bit-planes of the current iteration (ny x wpr words each)
   uint32_t* p_lo;
   uint32_t* p_cand;
-  float* ntab;       // uint16 frames: N for every integer med5 value 0..65535
+  float2* ntab;      // uint16 frames: {2N, RN(1/(2N))} for every integer med5 value 0..65535
   uint8_t* tflags;   // per core tile: [2][tiles] "recompute at level k" (buffer k & 1), [tiles] sticky
   uint8_t* mask_out;
   float* clean_out;  // the working image I, and the cleaned output
@@ -371,14 +373,53 @@ __device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
   return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
 }
 
-// N for every integer med5 value of a uint16 frame (the same arithmetic as
-// noise_of, evaluated once per value instead of once per pixel).
+// {D, y} = {2N, RN(1/D)} for an integer med5 value m (N with the same
+// arithmetic as noise_of; doubling is exact).
+__device__ __forceinline__ float2 ntab_entry(const FrameDesc& f, int m) {
+  const float N = noise_of(f, (float)m);
+  const float D = __fadd_rn(N, N);
+  return make_float2(D, __fdiv_rn(1.0f, D));
+}
+
+// The table of a uint16 frame, once per request instead of once per pixel.
 __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
   const int fi = blockIdx.y;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= nframes || m > 65535) return;
   const FrameDesc& f = fr[fi];
-  if (f.dtype == 1) f.ntab[m] = noise_of(f, (float)m);
+  if (f.dtype == 1) f.ntab[m] = ntab_entry(f, m);
+}
+
+// L / D rounded to nearest, for D > 0, L >= 0 and y = RN(1/D), without a
+// divide: Markstein's correction (P. Markstein, "Computation of elementary
+// functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34(1),
+// 1990).  q0 = RN(L y) can be off by more than an ulp; one correction
+// q1 = RN(q0 + r0 y), with r0 = L - D q0 from one fused multiply-add, makes
+// it faithful; then the remainder r1 = L - D q1 is exact and, y being
+// within half an ulp of 1/D, q1 + r1 y rounds to the correctly rounded
+// quotient.  The identity with IEEE division is checked exhaustively over
+// every L a uint16 frame's L+ can take (multiples of 1/4 up to 131070) and
+// every table entry by lacos_selftest_division.
+__device__ __forceinline__ float div_recip(float L, float D, float y) {
+  const float q0 = __fmul_rn(L, y);
+  const float r0 = __fmaf_rn(-q0, D, L);
+  const float q1 = __fmaf_rn(r0, y, q0);
+  const float r1 = __fmaf_rn(-q1, D, L);
+  return __fmaf_rn(r1, y, q1);
+}
+
+// Exhaustive check of div_recip against IEEE division: table entry m per
+// block, every L = k/4 with k = 0..524280 (the range of a uint16 frame's L+:
+// each of its four clipped terms is at most 2 * 65535) per thread stride.
+__global__ void selftest_division_kernel(FrameDesc f, unsigned long long* mismatches) {
+  const float2 t = ntab_entry(f, (int)blockIdx.x);
+  unsigned cnt = 0;
+  for (int k = threadIdx.x; k <= 4 * 131070; k += blockDim.x) {
+    const float L = __fmul_rn((float)k, 0.25f);
+    cnt += __float_as_uint(div_recip(L, t.x, t.y)) != __float_as_uint(__fdiv_rn(L, t.x)) ? 1u : 0u;
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(mismatches, (unsigned long long)cnt);
 }
 
 __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, float rt) {
@@ -415,7 +456,7 @@ template <> struct CoreSmemT<uint16_t> {
   uint8_t Mb[XR6::N];
   uint32_t Mw[TH + 12][MWORDS];
   float S[Reg<2>::N];
-  float N2[Reg<2>::N];           // N on R2 (the table at med5(I))
+  float2 DY[Reg<2>::N];          // {2N, 1/(2N)} on R2 (the table at med5(I))
   uint16_t M3[Reg<3>::N];
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
@@ -425,14 +466,14 @@ template <> struct CoreSmemT<uint16_t> {
 };
 static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list array");
 // Alignment of the vector accesses: 16-byte staging rows (X; Mb in 8-byte
-// groups), 4-pixel block-network loads, 2-pixel pairs of S, N/N2 and flags.
+// groups), 4-pixel block-network loads, 2-pixel pairs of S, N, DY and flags.
 template <class T>
 constexpr bool core_layout_ok() {
   return offsetof(T, X) % 16 == 0 && offsetof(T, Mb) % 8 == 0 && offsetof(T, S) % 8 == 0 &&
          offsetof(T, flags) % 4 == 0;
 }
 static_assert(core_layout_ok<CoreSmemT<float>>() && core_layout_ok<CoreSmemT<uint16_t>>(), "core layout");
-static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, N2) % 8 == 0,
+static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, DY) % 16 == 0,
               "core layout");
 // Dynamic shared memory of a core launch, by working-image type.
 template <class XT>
@@ -583,7 +624,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 // blocks per register -- a block in the upper half of the region with the
 // block the same distance further down -- so each min/max instruction
 // serves two outputs.  Each med5 indexes the N table right away (the
-// block's 16 loads are in flight together); N goes to N2.
+// block's 16 loads are in flight together); {2N, 1/(2N)} goes to DY.
 __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t>& sm) {
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_PAIRS = (TH + 4) / S_BH / 2;
   constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
@@ -608,7 +649,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
           for (int cc = 0; cc < S_BW; ++cc)
-            sm.N2[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = __ldg(f.ntab + half_of(m5[r * S_BW + cc], h));
+            sm.DY[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = __ldg(f.ntab + half_of(m5[r * S_BW + cc], h));
     } else {
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
@@ -678,33 +719,33 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
     if (q >= NP) break;
     const int ly = q / PW - 2, lx = (q % PW) * 2 - 2;
     const int c = XR6::idx(ly, lx), i2 = Reg<2>::idx(ly, lx);
-    float L0, L1, N0, N1;
+    float S0, S1;
     if constexpr (kU16) {
       const auto ld2 = [&](int o) { return *reinterpret_cast<const uint32_t*>(sm.X + o); };
       const uint32_t mid = ld2(c), lft = ld2(c - 2), rgt = ld2(c + 2);
       const uint32_t up = ld2(c - XR6::W), dn = ld2(c + XR6::W);
       const int v0 = (int)(mid & 0xffffu), v1 = (int)(mid >> 16);
-      L0 = lplus_int(v0, (int)(up & 0xffffu), (int)(dn & 0xffffu), (int)(lft >> 16), v1);
-      L1 = lplus_int(v1, (int)(up >> 16), (int)(dn >> 16), v0, (int)(rgt & 0xffffu));
-      const float2 nn = *reinterpret_cast<const float2*>(sm.N2 + i2);
-      N0 = nn.x;
-      N1 = nn.y;
+      const float L0 = lplus_int(v0, (int)(up & 0xffffu), (int)(dn & 0xffffu), (int)(lft >> 16), v1);
+      const float L1 = lplus_int(v1, (int)(up >> 16), (int)(dn >> 16), v0, (int)(rgt & 0xffffu));
+      const float4 dy = *reinterpret_cast<const float4*>(sm.DY + i2);  // {D0, y0, D1, y1}
+      S0 = div_recip(L0, dy.x, dy.y);
+      S1 = div_recip(L1, dy.z, dy.w);
     } else {
       const auto ld2 = [&](int o) { return *reinterpret_cast<const float2*>(sm.X + o); };
       const float2 mid = ld2(c), lft = ld2(c - 2), rgt = ld2(c + 2);
       const float2 up = ld2(c - XR6::W), dn = ld2(c + XR6::W);
-      L0 = lplus(mid.x, up.x, dn.x, lft.y, mid.y);
-      L1 = lplus(mid.y, up.y, dn.y, mid.x, rgt.x);
+      const float L0 = lplus(mid.x, up.x, dn.x, lft.y, mid.y);
+      const float L1 = lplus(mid.y, up.y, dn.y, mid.x, rgt.x);
       const float2 m = *reinterpret_cast<const float2*>(sm.S + i2);
-      N0 = noise_of(f, m.x);
-      N1 = noise_of(f, m.y);
+      const float N0 = noise_of(f, m.x), N1 = noise_of(f, m.y);
+      S0 = __fdiv_rn(L0, __fadd_rn(N0, N0));
+      S1 = __fdiv_rn(L1, __fadd_rn(N1, N1));
+      if (ly >= 0 && ly < TH && lx >= 0 && lx < TW)
+        *reinterpret_cast<float2*>(sm.N + ly * TW + lx) = make_float2(N0, N1);
     }
-    const float S0 = __fdiv_rn(L0, __fadd_rn(N0, N0));
-    const float S1 = __fdiv_rn(L1, __fadd_rn(N1, N1));
     *reinterpret_cast<float2*>(sm.S + i2) = make_float2(S0, S1);
     if (ly >= 0 && ly < TH && lx >= 0 && lx < TW) {
       const int t = ly * TW + lx;
-      if constexpr (!kU16) *reinterpret_cast<float2*>(sm.N + t) = make_float2(N0, N1);
       const uint32_t fl = *reinterpret_cast<const uint16_t*>(sm.flags + t);  // from sat_flags
       const bool sat0 = (fl & 8u) != 0, sat1 = (fl & 0x800u) != 0;
       if ((oy + ly) < f.ny) {
@@ -864,7 +905,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
-      N = sm.N2[c];
+      N = __fmul_rn(sm.DY[c].x, 0.5f);  // the table holds 2N; halving is exact
     else
       N = sm.N[i];
     float F = f.fnorm ? __fdiv_rn(diff, N) : diff;

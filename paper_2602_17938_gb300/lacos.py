@@ -88,8 +88,9 @@ def load_library():
         lib.lacos_get_core_variant.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
         lib.lacos_autotune.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P, P, I,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        lib.lacos_selftest_division.argtypes = [ctypes.c_float, ctypes.c_float, U64P]
         for name in ("lacos_submit_async", "lacos_set_core_variant", "lacos_get_core_variant",
-                     "lacos_autotune"):
+                     "lacos_autotune", "lacos_selftest_division"):
             getattr(lib, name).restype = I
         for name in ("lacos_create", "lacos_submit", "lacos_submit_batch", "lacos_poll",
                      "lacos_wait", "lacos_destroy", "lacos_last_cuda_error",
@@ -277,6 +278,17 @@ def clean_frame(frame, gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0
 
 
 STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def selftest_division(gain: float, readnoise: float) -> int:
+    """Pairs (numerator, table entry) where the uint16 path's division differs
+    from IEEE float32 division for these parameters (lacos_selftest_division)."""
+    lib = load_library()
+    out = ctypes.c_ulonglong()
+    rc = lib.lacos_selftest_division(float(gain), float(readnoise), ctypes.byref(out))
+    if rc != OK:
+        raise LacosError(rc, "lacos_selftest_division")
+    return int(out.value)
 
 
 def run_static(frame, params: Params, mask, clean, stream=None) -> FrameResult:
