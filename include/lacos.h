@@ -108,6 +108,24 @@ int lacos_submit_async(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny
                        const lacos_params *p, uint8_t *d_mask, float *d_clean,
                        unsigned long long *ticket);
 
+/* Host-to-host request: copies the host frame into device buffers the slot
+ * owns (charged to the budget, reused across requests), runs the request,
+ * and copies the mask and cleaned frame back into the host buffers, all on
+ * the slot's own stream; lacos_poll/lacos_wait report completion once the
+ * host outputs are written.  Requests submitted back to back use different
+ * slots and streams, so one frame's upload, another's compute and a third's
+ * download overlap (separate copy engines).
+ *   h_frame : in, ny*nx host pixels (LACOS_F32 float32 or LACOS_U16 uint16)
+ *   h_mask  : out, ny*nx uint8 host mask
+ *   h_clean : out, ny*nx float32 host cleaned frame
+ * Host buffers should be page-locked (cudaHostAlloc or registered) for the
+ * copies to overlap; the caller keeps them alive and leaves h_frame
+ * unchanged until completion.  Errors as lacos_submit (LACOS_EAGAIN when no
+ * slot or budget is free). */
+int lacos_submit_host(lacos_ctx *c, const void *h_frame, lacos_dtype dt, int ny, int nx,
+                      const lacos_params *p, uint8_t *h_mask, float *h_clean,
+                      unsigned long long *ticket);
+
 /* Non-blocking completion check.  Returns LACOS_PENDING while the request
  * runs; otherwise fills *res, releases the request's slot and returns
  * LACOS_OK (res->status carries LACOS_ENONFINITE/LACOS_ETIMEOUT if the device

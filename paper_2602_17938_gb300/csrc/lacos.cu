@@ -47,11 +47,20 @@ struct FrameReq {
   float* clean;
 };
 
+// Host buffers of a lacos_submit_host request.
+struct HostIO {
+  const void* frame;
+  uint8_t* mask;
+  float* clean;
+};
+
 struct Slot {
   bool busy = false;
   unsigned long long ticket = 0;
   void* dscratch = nullptr;  // device scratch
   size_t dcap = 0;
+  void* dio = nullptr;       // device copies of a host request's frame, mask and cleaned frame
+  size_t iocap = 0;
   void* hpinned = nullptr;   // pinned host staging (descriptors in, states out)
   size_t hcap = 0;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
@@ -175,6 +184,12 @@ static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
       sl.dscratch = nullptr;
       sl.dcap = 0;
       if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; sl.graph_key.clear(); }
+    }
+    if (!sl.busy && sl.dio && c->charged + need > c->budget) {
+      cudaFreeAsync(sl.dio, s);
+      c->charged -= sl.iocap;
+      sl.dio = nullptr;
+      sl.iocap = 0;
     }
   }
 }
@@ -301,16 +316,21 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   return LACOS_OK;
 }
 
-static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream_t s,
+static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStream_t s,
                        int reuse_graph, lacos_result* per_frame, unsigned long long* ticket,
-                       bool own_stream = false) {
-  if (!c || !ticket || fr.empty()) return LACOS_EINVAL;
-  for (const auto& f : fr)
+                       bool own_stream = false, const HostIO* hio = nullptr) {
+  if (!c || !ticket || fr_in.empty()) return LACOS_EINVAL;
+  for (const auto& f : fr_in)
     if (!frame_valid(f)) return LACOS_EINVAL;
+  std::vector<FrameReq> fr = fr_in;
   const Layout L = layout_for(fr);
+  // A host request (one frame) also needs device copies of its frame and outputs.
+  const size_t npx = hio ? (size_t)fr[0].ny * fr[0].nx : 0;
+  const size_t io_frame = align_up(npx * (fr[0].dtype == LACOS_U16 ? 2 : 4)), io_mask = align_up(npx);
+  const size_t io_need = hio ? io_frame + io_mask + align_up(npx * sizeof(float)) : 0;
   const size_t hneed = align_up(sizeof(FrameDesc) * fr.size()) + sizeof(FrameState) * fr.size();
   std::lock_guard<std::mutex> lk(c->mu);
-  if (L.total > c->budget) return LACOS_ENOMEM;
+  if (L.total + io_need > c->budget) return LACOS_ENOMEM;
   CK(cudaSetDevice(c->device));
   // Pick a free slot, preferring one whose scratch is already large enough.
   Slot* sl = nullptr;
@@ -337,6 +357,25 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream
     CK(cudaMallocAsync(&sl->dscratch, L.total, s));
     sl->dcap = L.total;
     c->charged += L.total;
+  }
+  if (sl->iocap < io_need) {
+    if (sl->dio) {
+      CK(cudaFreeAsync(sl->dio, s));
+      c->charged -= sl->iocap;
+      sl->dio = nullptr;
+      sl->iocap = 0;
+    }
+    evict_idle(c, io_need, s);
+    if (c->charged + io_need > c->budget) return LACOS_EAGAIN;
+    CK(cudaMallocAsync(&sl->dio, io_need, s));
+    sl->iocap = io_need;
+    c->charged += io_need;
+  }
+  if (hio) {  // the request reads and writes the slot's device copies
+    char* io = (char*)sl->dio;
+    fr[0].frame = io;
+    fr[0].mask = (uint8_t*)(io + io_frame);
+    fr[0].clean = (float*)(io + io_frame + io_mask);
   }
   if (sl->hcap < hneed) {
     if (sl->hpinned) { CK(cudaStreamSynchronize(s)); cudaFreeHost(sl->hpinned); }
@@ -372,8 +411,15 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr, cudaStream
     sl->prof_n = -1;
     CK(cudaGraphLaunch(sl->gexec, s));
   } else {
+    if (hio)
+      CK(cudaMemcpyAsync((void*)fr[0].frame, hio->frame, npx * (fr[0].dtype == LACOS_U16 ? 2 : 4),
+                         cudaMemcpyHostToDevice, s));
     rc = enqueue(c, *sl, fr, L, s, c->profiling);
     if (rc != LACOS_OK) return rc;
+    if (hio) {
+      CK(cudaMemcpyAsync(hio->mask, fr[0].mask, npx, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hio->clean, fr[0].clean, npx * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
   }
   CK(cudaEventRecord(sl->ev_done, s));
   sl->busy = true;
@@ -520,6 +566,16 @@ int lacos_submit_async(lacos_ctx* c, const void* d_frame, lacos_dtype dt, int ny
   return submit_impl(c, fr, nullptr, 0, nullptr, ticket, true);
 }
 
+int lacos_submit_host(lacos_ctx* c, const void* h_frame, lacos_dtype dt, int ny, int nx,
+                      const lacos_params* p, uint8_t* h_mask, float* h_clean,
+                      unsigned long long* ticket) {
+  if (!p || !h_frame || !h_mask || !h_clean) return LACOS_EINVAL;
+  // Placeholder device pointers pass validation; the slot's copies replace them.
+  std::vector<FrameReq> fr{{h_frame, (int)dt, ny, nx, *p, h_mask, h_clean}};
+  const HostIO hio{h_frame, h_mask, h_clean};
+  return submit_impl(c, fr, nullptr, 0, nullptr, ticket, true, &hio);
+}
+
 int lacos_set_core_variant(lacos_ctx* c, int variant) {
   if (!c || variant < 0 || variant > 3) return LACOS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -615,6 +671,7 @@ int lacos_destroy(lacos_ctx* c) {
   for (auto& sl : c->slots) {
     if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
     if (sl.dscratch) cudaFree(sl.dscratch);
+    if (sl.dio) cudaFree(sl.dio);
     if (sl.hpinned) cudaFreeHost(sl.hpinned);
     if (sl.ev_start) cudaEventDestroy(sl.ev_start);
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);

@@ -89,8 +89,9 @@ def load_library():
         lib.lacos_autotune.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P, P, I,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         lib.lacos_selftest_division.argtypes = [ctypes.c_float, ctypes.c_float, U64P]
+        lib.lacos_submit_host.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P, U64P]
         for name in ("lacos_submit_async", "lacos_set_core_variant", "lacos_get_core_variant",
-                     "lacos_autotune", "lacos_selftest_division"):
+                     "lacos_autotune", "lacos_selftest_division", "lacos_submit_host"):
             getattr(lib, name).restype = I
         for name in ("lacos_create", "lacos_submit", "lacos_submit_batch", "lacos_poll",
                      "lacos_wait", "lacos_destroy", "lacos_last_cuda_error",
@@ -162,6 +163,19 @@ class Context:
                                          ctypes.c_void_p(clean.data_ptr()), ctypes.byref(t))
         if rc != OK:
             raise LacosError(rc, "lacos_submit_async")
+        return t.value
+
+    def submit_host(self, h_frame, params: Params, h_mask, h_clean) -> int:
+        """Queue a host-to-host request (lacos_submit_host): CPU tensors, page-locked
+        for overlap; the outputs are written when the request completes.  Raises
+        LacosError(EAGAIN) when no slot or budget is free."""
+        ny, nx = h_frame.shape
+        t = ctypes.c_ulonglong(0)
+        rc = self.lib.lacos_submit_host(self.h, ctypes.c_void_p(h_frame.data_ptr()), _dtype_code(h_frame),
+                                        ny, nx, ctypes.byref(params), ctypes.c_void_p(h_mask.data_ptr()),
+                                        ctypes.c_void_p(h_clean.data_ptr()), ctypes.byref(t))
+        if rc != OK:
+            raise LacosError(rc, "lacos_submit_host")
         return t.value
 
     def set_core_variant(self, v: int):
@@ -311,26 +325,26 @@ def run_static(frame, params: Params, mask, clean, stream=None) -> FrameResult:
     return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms)
 
 
-def clean_host(h_frame, params: Params, h_mask, h_clean, ctx: Context, work=None, stream=None):
-    """Host-to-host detect-and-clean: copy a (pinned) host frame to the device,
-    run it, and copy the mask and cleaned frame back; returns FrameResult.
-    ``work`` = (d_frame, d_mask, d_clean) device buffers to reuse (else allocated)."""
-    import torch
-    if work is None:
-        work = (torch.empty(h_frame.shape, dtype=h_frame.dtype, device="cuda"),
-                torch.empty(h_frame.shape, dtype=torch.uint8, device="cuda"),
-                torch.empty(h_frame.shape, dtype=torch.float32, device="cuda"))
-    d_frame, d_mask, d_clean = work
-    if d_frame.dtype == torch.uint16:  # same bits; int16 copies are supported everywhere
-        d_frame.view(torch.int16).copy_(h_frame.view(torch.int16), non_blocking=True)
-    else:
-        d_frame.copy_(h_frame, non_blocking=True)
-    t = ctx.submit(d_frame, params, d_mask, d_clean, stream)
-    h_mask.copy_(d_mask, non_blocking=True)
-    h_clean.copy_(d_clean, non_blocking=True)
-    res = ctx.wait(t)
-    (stream or torch.cuda.current_stream()).synchronize()
-    return res
+def clean_host(h_frame, params: Params, h_mask, h_clean, ctx: Context):
+    """Host-to-host detect-and-clean of one frame through lacos_submit_host:
+    the library copies the (page-locked) host frame in and the mask and cleaned
+    frame out.  Returns FrameResult."""
+    return ctx.wait(ctx.submit_host(h_frame, params, h_mask, h_clean))
+
+
+def clean_host_stream(ctx: Context, frames, params: Params, masks, cleans, depth: int = 3):
+    """Host-to-host detect-and-clean of a sequence of frames, up to ``depth``
+    requests in flight (one frame's upload, another's compute and a third's
+    download overlap).  Returns the FrameResults in order."""
+    pending, results = [], [None] * len(frames)
+    for i, (f, m, c) in enumerate(zip(frames, masks, cleans)):
+        if len(pending) >= depth:
+            j, t = pending.pop(0)
+            results[j] = ctx.wait(t)
+        pending.append((i, ctx.submit_host(f, params, m, c)))
+    for j, t in pending:
+        results[j] = ctx.wait(t)
+    return results
 
 
 def to_device(frame: np.ndarray, device="cuda"):

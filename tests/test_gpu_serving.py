@@ -127,3 +127,38 @@ def test_every_core_variant_bit_exact_and_autotune(lib, dtype, tmp_path, monkeyp
         assert 0 <= best <= 3 and ctx.core_variant() == best and len(ms) == 4
         best2, ms2 = autotune.tune(ctx, d, p, m, c)  # from the cache
         assert best2 == best and ms2 is None
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint16])
+def test_host_requests_match_device_requests(lib, dtype):
+    lacos = lib
+    frames = [_frame(ny, nx, 70 + i, dtype) for i, (ny, nx) in enumerate([(300, 410), (517, 260), (96, 1000)])]
+    p = lacos.make_params(1.1, 1.4, niter=4)
+    tdt = torch.uint16 if dtype == np.uint16 else torch.float32
+    with lacos.Context(0) as ctx:
+        ref = []
+        for f in frames:
+            d = lacos.to_device(f)
+            m = torch.empty(f.shape, dtype=torch.uint8, device="cuda")
+            c = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+            r = ctx.wait(ctx.submit(d, p, m, c))
+            ref.append((m.cpu(), c.cpu(), r))
+        h_frames = [torch.from_numpy(f.view(np.int16) if dtype == np.uint16 else f).pin_memory().view(tdt)
+                    for f in frames]
+        h_masks = [torch.zeros(f.shape, dtype=torch.uint8).pin_memory() for f in frames]
+        h_cleans = [torch.zeros(f.shape, dtype=torch.float32).pin_memory() for f in frames]
+        # one at a time, then streamed with two in flight (mixed sizes reuse the slots' buffers)
+        for i in range(len(frames)):
+            r = lacos.clean_host(h_frames[i], p, h_masks[i], h_cleans[i], ctx=ctx)
+            assert r.status == 0 and r.n_flagged == ref[i][2].n_flagged
+            assert torch.equal(h_masks[i], ref[i][0])
+            assert torch.equal(h_cleans[i].view(torch.int32), ref[i][1].view(torch.int32))
+            h_masks[i].zero_()
+            h_cleans[i].zero_()
+        order = [2, 0, 1, 2, 1, 0]
+        res = lacos.clean_host_stream(ctx, [h_frames[j] for j in order], p,
+                                      [h_masks[j] for j in order], [h_cleans[j] for j in order], depth=2)
+        assert [r.n_flagged for r in res] == [ref[j][2].n_flagged for j in order]
+        for i in range(len(frames)):
+            assert torch.equal(h_masks[i], ref[i][0])
+            assert torch.equal(h_cleans[i].view(torch.int32), ref[i][1].view(torch.int32))
