@@ -78,7 +78,7 @@ constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
 
 struct FrameState {
-  unsigned long long fresh[LACOS_MAX_NITER + 1];  // new pixels found by iteration k
+  unsigned long long fresh[LACOS_MAX_NITER + 1];  // nonzero when iteration k flagged new pixels
   unsigned long long flagged;                      // pixels in the final mask
   unsigned long long n_sprime, n_fine, n_replace;  // sparse-work counters (profiling)
   unsigned long long n_replace_wide;               // replacements whose 5x5 window was all flagged
@@ -773,8 +773,23 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
   warp_emit(hits, &sm.nlist, sm.list, Reg<4>::N - 1, tix);
 }
 
+// Work counters of a tile (valid in thread 0).  A block sums them over its
+// tiles and adds them to the frame's state once per frame it leaves, instead
+// of one same-address atomic per tile.
+struct TileCounts {
+  unsigned long long px = 0, sprime = 0, fine = 0, replace = 0;
+};
+
+__device__ __forceinline__ void flush_counts(FrameState* st, const TileCounts& c) {
+  if (!st) return;
+  if (c.px) atomicAdd(&st->px_core, c.px);
+  if (c.sprime) atomicAdd(&st->n_sprime, c.sprime);
+  if (c.fine) atomicAdd(&st->n_fine, c.fine);
+  if (c.replace) atomicAdd(&st->n_replace, c.replace);
+}
+
 template <class XT>
-__device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm) {
+__device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm) {
   using KT = KeyOf<XT>;
   using K = typename KT::K;
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
@@ -784,6 +799,7 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
   const int ny = f.ny, nx = f.nx;
   const bool edge = (oy - 6 < 0) || (ox - 6 < 0) || (oy + TH + 6 > ny) || (ox + TW + 6 > nx);
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
+  TileCounts counts;
 
   for (int i = tid; i < 3 * TH * TWW; i += NT) (&sm.pw[0][0][0])[i] = 0u;
   if (tid == 0) sm.nfine = 0;
@@ -834,7 +850,10 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
       }
       sm.X[c] = v;
     }
-    if (tid == 0) { sm.nlist = 0; if (n) atomicAdd(&f.st->n_replace, (unsigned long long)n); }
+    if (tid == 0) {
+      sm.nlist = 0;
+      counts.replace = n;
+    }
     __syncthreads();
     if (edge) {
       for (int i = tid; i < Reg<4>::N; i += NT) {
@@ -926,10 +945,11 @@ __device__ void core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm)
     }
   }
   if (tid == 0) {
-    atomicAdd(&f.st->px_core, (unsigned long long)(min(TH, ny - oy) * min(TW, nx - ox)));
-    if (total) atomicAdd(&f.st->n_sprime, (unsigned long long)total);
-    if (sm.nfine) atomicAdd(&f.st->n_fine, (unsigned long long)sm.nfine);
+    counts.px = (unsigned long long)(min(TH, ny - oy) * min(TW, nx - ox));
+    counts.sprime = total;
+    counts.fine = sm.nfine;
   }
+  return counts;
 }
 
 // MINB: resident CTAs per SM the register allocation is bounded for (the
@@ -945,6 +965,12 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
   __shared__ unsigned s_item;
   __shared__ int s_run;
   constexpr int kDtype = std::is_same<XT, uint16_t>::value ? 1 : 0;
+  __shared__ TileCounts acc;       // sums of the tiles of frame acc_st so far (thread 0)
+  __shared__ FrameState* acc_st;
+  if (threadIdx.x == 0) {
+    acc = TileCounts{};
+    acc_st = nullptr;
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned item = item_begin + atomicAdd(head, 1u);
@@ -969,9 +995,21 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
     if (item >= item_end) break;
     if (!run) continue;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    core_tile<XT>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<XT>*>(smem_raw));
+    const TileCounts c = core_tile<XT>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<XT>*>(smem_raw));
+    if (threadIdx.x == 0) {
+      if (f.st != acc_st) {
+        flush_counts(acc_st, acc);
+        acc = TileCounts{};
+        acc_st = f.st;
+      }
+      acc.px += c.px;
+      acc.sprime += c.sprime;
+      acc.fine += c.fine;
+      acc.replace += c.replace;
+    }
     __syncthreads();
   }
+  if (threadIdx.x == 0) flush_counts(acc_st, acc);
 }
 
 // ---- which core tiles a level must recompute -------------------------------
@@ -1036,7 +1074,6 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
   constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
   __shared__ uint32_t C[GB_H + 4][CW];
   __shared__ uint32_t G1[GB_H + 2][GW];
-  __shared__ unsigned s_cnt;
   const int tid = threadIdx.x;
   const unsigned blk = blockIdx.x;
   if (blk >= total_blocks) return;
@@ -1062,7 +1099,6 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
   }
   const uint32_t lo = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
   const uint32_t mp = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
-  if (tid == 0) s_cnt = 0;
 #pragma unroll
   for (int p = 0; p < CP; ++p) {
     const int i = p * NT + tid;
@@ -1081,7 +1117,7 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
     }
   }
   __syncthreads();
-  unsigned cnt = 0;
+  bool any = false;
   if (own) {
     uint32_t d2 = 0;
 #pragma unroll
@@ -1090,14 +1126,13 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
     uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
     Mn[(size_t)y * wpr + w] = mp | g2;
     const uint32_t fresh = g2 & ~mp;
-    cnt = __popc(fresh);
+    any = fresh != 0;
     if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((tid & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
-  __syncthreads();
-  if (tid == 0 && s_cnt) atomicAdd(&f.st->fresh[k], (unsigned long long)s_cnt);
+  // Only "did level k flag anything" is used (early stop): one flag store
+  // per block that found new pixels, skipped once some block has set it.
+  if (__syncthreads_or(any) && tid == 0 && !*(volatile unsigned long long*)&f.st->fresh[k])
+    f.st->fresh[k] = 1;
 }
 
 // ---- output: cleaned frame and uint8 mask of the last mask ----------------
@@ -1118,7 +1153,7 @@ constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
 // memory, and the tile is then written out coalesced, four pixels per
 // thread where the row pitch allows 16-byte stores.
 template <class XT>
-__device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
+__device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
   const int tid = threadIdx.x;
   const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
   const int run = run_of(f);
@@ -1174,10 +1209,8 @@ __device__ void finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
       }
     }
   }
-  if (tid == 0) {
-    if (n) atomicAdd(&f.st->flagged, (unsigned long long)n);
-    if (tix == 0) f.st->iters_run = run;
-  }
+  if (tid == 0 && tix == 0) f.st->iters_run = run;
+  return n;
 }
 
 __global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
@@ -1185,6 +1218,12 @@ __global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __rest
   __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
   __shared__ unsigned s_item;
   const int tid = threadIdx.x;
+  __shared__ unsigned long long flagged;  // flagged pixels of frame acc_st so far (thread 0)
+  __shared__ FrameState* acc_st;
+  if (tid == 0) {
+    flagged = 0;
+    acc_st = nullptr;
+  }
   for (;;) {
     if (tid == 0) s_item = atomicAdd(head, 1u);
     __syncthreads();
@@ -1192,19 +1231,29 @@ __global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __rest
     if (item >= total) break;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
     const int tix = (int)(item - f.tile_begin);
+    unsigned n;
     if (f.dtype == 1) {
       auto& sm = *reinterpret_cast<FinalSmemT<uint16_t>*>(smem);
       if (tid == 0) sm.nlist = 0;
       __syncthreads();
-      finalize_tile<uint16_t>(f, tix, sm);
+      n = finalize_tile<uint16_t>(f, tix, sm);
     } else {
       auto& sm = *reinterpret_cast<FinalSmemT<float>*>(smem);
       if (tid == 0) sm.nlist = 0;
       __syncthreads();
-      finalize_tile<float>(f, tix, sm);
+      n = finalize_tile<float>(f, tix, sm);
+    }
+    if (tid == 0) {
+      if (f.st != acc_st) {
+        if (acc_st && flagged) atomicAdd(&acc_st->flagged, flagged);
+        flagged = 0;
+        acc_st = f.st;
+      }
+      flagged += n;
     }
     __syncthreads();
   }
+  if (tid == 0 && acc_st && flagged) atomicAdd(&acc_st->flagged, flagged);
 }
 
 }  // namespace lacos
