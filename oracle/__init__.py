@@ -50,7 +50,7 @@ def _load():
             i, f, ll = ctypes.c_int, ctypes.c_float, ctypes.c_longlong
             for suf in ("f32", "f64"):
                 fn = getattr(lib, f"oracle_run_{suf}")
-                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, P, P, P, P]
+                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, i, P, P, P, P]
                 fn.restype = i
                 fn = getattr(lib, f"oracle_iterate_{suf}")
                 fn.argtypes = [P, P, i, i, f, f, f, f, f, i, P, P] + [P] * 12
@@ -67,6 +67,8 @@ def _load():
                 fn.restype = i
             lib.oracle_dilate3.argtypes = [P, i, i, P]
             lib.oracle_dilate3.restype = None
+            lib.oracle_dilate_square.argtypes = [P, i, i, i, P]
+            lib.oracle_dilate_square.restype = None
             _lib = lib
     return _lib
 
@@ -81,8 +83,9 @@ def _dt(precision: str):
 
 def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 65535.0,
         sigclip: float = 4.5, sigfrac: float = 0.3, objlim: float = 5.0, niter: int = 4,
-        fnorm: bool = True, precision: str = "f32"):
-    """Full detect-and-clean loop.  Returns (mask u8, cleaned, iters_run, n_flagged)."""
+        fnorm: bool = True, precision: str = "f32", satgrow: int = 0):
+    """Full detect-and-clean loop.  Returns (mask u8, cleaned, iters_run, n_flagged).
+    satgrow: radius of the protected square around saturated pixels (reading C16)."""
     lib = _load()
     frame = np.ascontiguousarray(frame)
     if frame.dtype == np.uint16:
@@ -99,7 +102,8 @@ def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 6553
     nf = ctypes.c_longlong(0)
     rc = getattr(lib, f"oracle_run_{suf}")(
         _ptr(frame), dtype, ny, nx, gain, readnoise, satlevel, sigclip, sigfrac, objlim,
-        int(niter), int(bool(fnorm)), _ptr(mask), _ptr(clean), ctypes.byref(it), ctypes.byref(nf))
+        int(niter), int(bool(fnorm)), int(satgrow), _ptr(mask), _ptr(clean), ctypes.byref(it),
+        ctypes.byref(nf))
     if rc != 0:
         raise ValueError(f"oracle_run_{suf} failed with code {rc}")
     return mask, clean, it.value, nf.value
@@ -159,6 +163,15 @@ def dilate3(B: np.ndarray):
     B = np.ascontiguousarray(B, np.uint8)
     out = np.zeros_like(B)
     lib.oracle_dilate3(_ptr(B), B.shape[0], B.shape[1], _ptr(out))
+    return out
+
+
+def dilate_square(B: np.ndarray, r: int):
+    """The saturated set grown by the square of radius r, inside the frame (C16)."""
+    lib = _load()
+    B = np.ascontiguousarray(B, np.uint8)
+    out = np.zeros_like(B)
+    lib.oracle_dilate_square(_ptr(B), B.shape[0], B.shape[1], int(r), _ptr(out))
     return out
 
 

@@ -150,8 +150,26 @@ template <class T>
 struct Params {
   T gain, readnoise, satlevel, sigclip, sigfrac, objlim;
   int niter;
-  int fnorm;  // 1: F = max((m3-m7)/N, 0.01) (reading C6); 0: F = max(m3-m7, 0.01)
+  int fnorm;    // 1: F = max((m3-m7)/N, 0.01) (reading C6); 0: F = max(m3-m7, 0.01)
+  int satgrow;  // reading C16: radius of the protected region around saturated pixels (0..4)
 };
+
+// Reading C16 (saturated-star protection, the paper's concern that centres
+// of (near-)saturated stars get taken for cosmic rays): the saturated set is
+// grown by the square of radius r (all pixels within Chebyshev distance r,
+// inside the frame), and every use of "saturated" -- never a candidate,
+// never grown into, so never replaced -- uses the grown set.  r = 0 leaves
+// reading C9 unchanged.
+void dilate_square(const uint8_t* in, int ny, int nx, int r, uint8_t* out) {
+  for (int i = 0; i < ny; ++i)
+    for (int j = 0; j < nx; ++j) {
+      uint8_t v = 0;
+      for (int a = std::max(0, i - r); a <= std::min(ny - 1, i + r) && !v; ++a)
+        for (int b = std::max(0, j - r); b <= std::min(nx - 1, j + r); ++b)
+          if (in[(size_t)a * nx + b]) { v = 1; break; }
+      out[(size_t)i * nx + j] = v;
+    }
+}
 
 // Ingest (a0): convert to T, canonicalise -0 to +0, reject non-finite input,
 // and mark saturated pixels (C9: original input >= satlevel, satlevel > 0).
@@ -266,11 +284,17 @@ int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_
         T* clean_out, int* iters_run, long long* n_flagged) {
   if (!frame || ny < 1 || nx < 1 || (dtype != 0 && dtype != 1)) return -1;
   if (!params_ok(p.gain, p.readnoise, p.sigclip, p.sigfrac, p.objlim, p.niter)) return -1;
+  if (p.satgrow < 0 || p.satgrow > 4) return -1;
   const size_t n = (size_t)ny * nx;
   std::vector<T> X0;
   std::vector<uint8_t> sat;
   const int rc = ingest(frame, dtype, n, p.satlevel, X0, sat);
   if (rc) return rc;
+  if (p.satgrow > 0) {
+    std::vector<uint8_t> grown(n);
+    dilate_square(sat.data(), ny, nx, p.satgrow, grown.data());
+    sat.swap(grown);
+  }
   std::vector<T> I(X0);
   std::vector<uint8_t> M(n, 0);
   int k = 0;
@@ -293,11 +317,11 @@ int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_
 
 template <class T>
 Params<T> make_params(double gain, double rn, double satlevel, double sigclip, double sigfrac,
-                      double objlim, int niter, int fnorm) {
+                      double objlim, int niter, int fnorm, int satgrow) {
   Params<T> p;
   p.gain = (T)gain; p.readnoise = (T)rn; p.satlevel = (T)satlevel;
   p.sigclip = (T)sigclip; p.sigfrac = (T)sigfrac; p.objlim = (T)objlim;
-  p.niter = niter; p.fnorm = fnorm;
+  p.niter = niter; p.fnorm = fnorm; p.satgrow = satgrow;
   return p;
 }
 
@@ -312,18 +336,19 @@ extern "C" {
 
 int oracle_run_f32(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
-                   int fnorm, uint8_t* mask, float* clean, int* iters_run, long long* n_flagged) {
+                   int fnorm, int satgrow, uint8_t* mask, float* clean, int* iters_run,
+                   long long* n_flagged) {
   return run<float>(frame, dtype, ny, nx,
-                    make_params<float>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm),
+                    make_params<float>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow),
                     mask, clean, iters_run, n_flagged);
 }
 
 int oracle_run_f64(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
-                   int fnorm, uint8_t* mask, double* clean, int* iters_run,
+                   int fnorm, int satgrow, uint8_t* mask, double* clean, int* iters_run,
                    long long* n_flagged) {
   return run<double>(frame, dtype, ny, nx,
-                     make_params<double>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm),
+                     make_params<double>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow),
                      mask, clean, iters_run, n_flagged);
 }
 
@@ -334,7 +359,7 @@ int oracle_run_f64(const void* frame, int dtype, int ny, int nx, float gain, flo
                                  float rn, float sigclip, float sigfrac, float objlim, int fnorm, \
                                  T* I, uint8_t* M, T* L, T* m5, T* N, T* S, T* mS, T* Sp, T* m3,  \
                                  T* m7, T* F, uint8_t* cand, uint8_t* g1, uint8_t* g2) {         \
-    Params<T> p = make_params<T>(gain, rn, 0.0, sigclip, sigfrac, objlim, 1, fnorm);             \
+    Params<T> p = make_params<T>(gain, rn, 0.0, sigclip, sigfrac, objlim, 1, fnorm, 0);          \
     Dumps<T> d{L, m5, N, S, mS, Sp, m3, m7, F, cand, g1, g2};                                     \
     return iterate<T>(X0, sat, ny, nx, p, I, M, &d);                                              \
   }
@@ -356,6 +381,9 @@ void oracle_median_f64(const double* A, int ny, int nx, int K, double* out) {
   median_filter(A, ny, nx, K, out);
 }
 void oracle_dilate3(const uint8_t* in, int ny, int nx, uint8_t* out) { dilate3(in, ny, nx, out); }
+void oracle_dilate_square(const uint8_t* in, int ny, int nx, int r, uint8_t* out) {
+  dilate_square(in, ny, nx, r, out);
+}
 int oracle_maskmed_f32(const float* X0, const uint8_t* M, int ny, int nx, int i, int j,
                        float* out) {
   return maskmed(X0, M, ny, nx, i, j, out) ? 0 : 1;

@@ -291,6 +291,55 @@ def test_saturated_pixels_never_flagged():
     assert m2[50, 50] == 1
 
 
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 4])
+def test_saturation_region_is_the_square_dilation(r):
+    # Reading C16: the saturated set grown by the (2r+1)^2 square, inside the frame --
+    # scipy's binary dilation with that structuring element and a zero border.
+    rng = np.random.default_rng(100 + r)
+    for shape in [(1, 1), (1, 9), (7, 1), (23, 31), (64, 50)]:
+        B = (rng.random(shape) < 0.03).astype(np.uint8)
+        B[0, 0] = 1  # a corner seed
+        ref = ndimage.binary_dilation(B, structure=np.ones((2 * r + 1, 2 * r + 1), bool)) if r else B
+        assert np.array_equal(oracle.dilate_square(B, r), ref.astype(np.uint8)), (shape, r)
+
+
+def test_satgrow_zero_is_reading_c9():
+    f, sig = _noise_frame(13, 96, 96)
+    f[20:23, 30:33] = 65535.0
+    f[40, 70] += 80 * sig
+    a = oracle.run(f, 1.0, 1.5, satlevel=65535.0)
+    b = oracle.run(f, 1.0, 1.5, satlevel=65535.0, satgrow=0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2:] == b[2:]
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_nothing_flagged_in_the_grown_saturated_region(r):
+    rng = np.random.default_rng(7 * r)
+    f, sig = _noise_frame(14 + r, 128, 128)
+    for _ in range(6):  # saturated star cores
+        y, x = rng.integers(8, 120, 2)
+        f[y - 1:y + 2, x - 1:x + 2] = 65535.0
+    hits = rng.integers(0, 128, (300, 2))
+    f[hits[:, 0], hits[:, 1]] += rng.uniform(40, 400, 300) * sig
+    sat0 = (f >= 65535.0).astype(np.uint8)
+    m, c, it, nf = oracle.run(f, 1.0, 1.5, satlevel=65535.0, satgrow=r)
+    grown = ndimage.binary_dilation(sat0, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+    assert not (m.astype(bool) & grown).any()
+    assert np.array_equal(c[grown], f[grown])  # never replaced
+    assert nf > 0  # hits elsewhere are still found
+
+
+def test_satgrow_protects_a_hit_next_to_a_saturated_core():
+    f, sig = _noise_frame(15, 96, 96)
+    f[40:43, 40:43] = 65535.0  # saturated star core
+    f[41, 45] += 80 * sig  # an ordinary hit 3 px right of the core's edge column
+    m0, *_ = oracle.run(f, 1.0, 1.5, satlevel=65535.0)
+    m2, *_ = oracle.run(f, 1.0, 1.5, satlevel=65535.0, satgrow=2)
+    m3, *_ = oracle.run(f, 1.0, 1.5, satlevel=65535.0, satgrow=3)
+    assert m0[41, 45] == 1 and m2[41, 45] == 1  # distance 3 from the core: outside r = 2
+    assert m3[41, 45] == 0
+
+
 def _config0():
     from paper_2602_17938_gb300 import synth
     spec = synth.config_specs(0)[0]
