@@ -66,11 +66,16 @@ enum {
  * gain > 0 [e-/ADU]; readnoise >= 0 [e-]; satlevel [ADU], <= 0 disables the
  * saturation guard; sigclip, sigfrac, objlim > 0; 0 <= niter <= 256.
  * fine_norm: 1 divides the fine-structure image by N (default reading),
- * 0 uses max(med3 - med7, 0.01) unnormalised. */
+ * 0 uses max(med3 - med7, 0.01) unnormalised.
+ * satgrow: 0..4, saturated-star protection: the pixels within this many
+ * pixels (Chebyshev distance) of a saturated input pixel are treated as
+ * saturated too (never flagged, never replaced); 0 protects only the
+ * saturated pixels themselves. */
 typedef struct {
   float gain, readnoise, satlevel, sigclip, sigfrac, objlim;
   int niter;
   int fine_norm;
+  int satgrow;
 } lacos_params;
 
 typedef struct {

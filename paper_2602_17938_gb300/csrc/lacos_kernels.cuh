@@ -103,6 +103,7 @@ struct FrameDesc {
   FrameState* st;
   float gain, rn2, satlevel, sigclip, lo, thr_min, objlim;
   int niter, fnorm;
+  int satgrow;       // radius of the protected region around saturated pixels (0..4)
   int tiles_x;
   unsigned int tile_begin, tile_end;    // this frame's range in the flattened tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
@@ -520,6 +521,40 @@ struct QuadLoaderU16 {
   }
 };
 
+// Saturation flags with protection radius r = satgrow > 0: the seeds (the
+// original input >= satlevel at an unflagged pixel) on the tile + r, then an
+// OR over columns -r..r and one over rows -r..r.  Out-of-frame positions hold
+// clamped copies, which add no seed an in-frame position does not hold
+// closer.  All threads; the list array is free scratch here.
+template <class XT, class SM>
+__device__ __forceinline__ void sat_grown(const FrameDesc& f, SM& sm) {
+  const int r = f.satgrow;
+  const int W = TW + 2 * r, H = TH + 2 * r;
+  uint8_t* seed = reinterpret_cast<uint8_t*>(sm.list);  // H x W, from (-r, -r)
+  uint8_t* hor = seed + (TH + 8) * (TW + 8);             // H x TW, from (-r, 0)
+  static_assert((TH + 8) * (TW + 8) + (TH + 8) * TW <= (int)sizeof(sm.list), "satgrow scratch");
+  const bool chk = f.satlevel > 0.0f;
+  for (int i = threadIdx.x; i < H * W; i += NT) {
+    const int c = XR6::idx(i / W - r, i % W - r);
+    seed[i] = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H * TW; i += NT) {
+    const uint8_t* s = seed + (i / TW) * W + i % TW;  // columns lx-r .. lx+r
+    uint8_t v = 0;
+    for (int d = 0; d <= 2 * r; ++d) v |= s[d];
+    hor[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < TH * TW; i += NT) {
+    const uint8_t* h = hor + i;  // rows ly-r .. ly+r
+    uint8_t v = 0;
+    for (int d = 0; d <= 2 * r; ++d) v |= h[d * TW];
+    sm.flags[i] = v ? 8 : 0;
+  }
+  __syncthreads();
+}
+
 // Assignment of the dense step's block units to (round, thread): the med5
 // units first, the med3 units after them starting at a warp boundary, so
 // that no warp runs both kinds (a warp with both would execute the two
@@ -552,6 +587,7 @@ __device__ __forceinline__ void sat_flags(const FrameDesc& f, SM& sm) {
   static_assert(FIRST >= 0 && FIRST < NT, "some threads must take the flags");
   constexpr int first = FIRST;
   const int tid = (int)threadIdx.x;
+  if (f.satgrow) return;  // the grown region is formed after the networks (sat_grown)
   if (tid < first) return;
   const bool chk = f.satlevel > 0.0f;
   for (int q = tid - first; q < TH * TW / 4; q += NT - first) {
@@ -874,6 +910,7 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     dense_f32(f, sm);
   if (tid == 0) sm.nlist2 = 0;
   __syncthreads();
+  if (f.satgrow) sat_grown<XT>(f, sm);
   dense_pixels(f, sm, oy, ox);
   __syncthreads();
   if (edge) {

@@ -122,6 +122,27 @@ def test_dense_hits_exercise_widened_replacement(ctx):
         assert full.any(), "test frame no longer reaches the widened replacement"
 
 
+@pytest.mark.parametrize("r", [1, 2, 4])
+@pytest.mark.parametrize("dtype", [np.float32, np.uint16])
+def test_saturated_star_protection(ctx, r, dtype):
+    # Saturated star cores, some on tile borders and frame edges, with hits
+    # scattered around them: the grown protected region (reading C16) must
+    # match the oracle bit for bit.
+    rng = np.random.default_rng(40 + r)
+    f = noisy_with_hits(150, 260, seed=90 + r, n_hits=400).astype(np.float64)
+    for (y, x) in [(30, 62), (31, 130), (64, 5), (100, 200), (148, 258), (2, 100), (75, 64)]:
+        f[max(0, y - 1):y + 2, max(0, x - 1):x + 2] = 65535.0
+        for _ in range(6):  # hits around each core
+            dy, dx = rng.integers(-6, 7, 2)
+            yy, xx = min(max(y + dy, 0), 149), min(max(x + dx, 0), 259)
+            if f[yy, xx] < 65535.0:
+                f[yy, xx] += rng.uniform(400, 3000)
+    frame = np.clip(np.rint(f), 0, 65535).astype(np.uint16) if dtype == np.uint16 else f.astype(np.float32)
+    m_ref, _ = assert_same(frame, 1.0, 1.5, gpu_run(ctx, frame, 1.0, 1.5, satgrow=r), satgrow=r)
+    m0, *_ = oracle.run(frame, 1.0, 1.5)
+    assert (m0.astype(int) - m_ref.astype(int)).max() == 1, "the protection should remove some flags"
+
+
 def test_varied_parameters(ctx):
     f = noisy_with_hits(140, 160, seed=8)
     for kw in ({"sigclip": 3.0, "sigfrac": 0.5, "objlim": 2.0}, {"sigclip": 6.0, "sigfrac": 1.5, "objlim": 8.0},
@@ -143,7 +164,7 @@ def test_argument_errors(ctx):
     m = torch.empty((16, 16), dtype=torch.uint8, device="cuda")
     c = torch.empty((16, 16), dtype=torch.float32, device="cuda")
     for bad in (dict(gain=0.0), dict(gain=-1.0), dict(sigclip=0.0), dict(niter=-1), dict(niter=257),
-                dict(readnoise=-1.0), dict(objlim=float("nan"))):
+                dict(readnoise=-1.0), dict(objlim=float("nan")), dict(satgrow=-1), dict(satgrow=5)):
         kw = dict(gain=1.0, readnoise=1.5)
         kw.update(bad)
         with pytest.raises(lacos.LacosError) as e:
