@@ -471,7 +471,7 @@ static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list
 template <class T>
 constexpr bool core_layout_ok() {
   return offsetof(T, X) % 16 == 0 && offsetof(T, Mb) % 8 == 0 && offsetof(T, S) % 8 == 0 &&
-         offsetof(T, flags) % 4 == 0;
+         offsetof(T, flags) % 8 == 0;
 }
 static_assert(core_layout_ok<CoreSmemT<float>>() && core_layout_ok<CoreSmemT<uint16_t>>(), "core layout");
 static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, DY) % 16 == 0,
@@ -521,36 +521,55 @@ struct QuadLoaderU16 {
   }
 };
 
-// Saturation flags with protection radius r = satgrow > 0: the seeds (the
-// original input >= satlevel at an unflagged pixel) on the tile + r, then an
-// OR over columns -r..r and one over rows -r..r.  Out-of-frame positions hold
+// Saturation flags with protection radius r = satgrow > 0 (1..4): the seeds
+// (the original input >= satlevel at an unflagged pixel) of each row of the
+// tile + r as bits, by ballot over the staged columns -8..87 (those outside
+// -8..71 are not staged and hold no seed); the OR over columns -r..r by
+// shifts of the 128-bit row; then, per tile row and 8-column group, the OR
+// over rows -r..r expanded to flag bytes.  Out-of-frame positions hold
 // clamped copies, which add no seed an in-frame position does not hold
 // closer.  All threads; the list array is free scratch here.
 template <class XT, class SM>
 __device__ __forceinline__ void sat_grown(const FrameDesc& f, SM& sm) {
   const int r = f.satgrow;
-  const int W = TW + 2 * r, H = TH + 2 * r;
-  uint8_t* seed = reinterpret_cast<uint8_t*>(sm.list);  // H x W, from (-r, -r)
-  uint8_t* hor = seed + (TH + 8) * (TW + 8);             // H x TW, from (-r, 0)
-  static_assert((TH + 8) * (TW + 8) + (TH + 8) * TW <= (int)sizeof(sm.list), "satgrow scratch");
+  uint64_t* hrow = reinterpret_cast<uint64_t*>(sm.list);  // rows -r .. TH+r-1: bit x = column x
+  static_assert((TH + 8) * sizeof(uint64_t) <= sizeof(sm.list) && TW == 64, "satgrow scratch");
   const bool chk = f.satlevel > 0.0f;
-  for (int i = threadIdx.x; i < H * W; i += NT) {
-    const int c = XR6::idx(i / W - r, i % W - r);
-    seed[i] = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int row = warp; row < TH + 2 * r; row += NT / 32) {
+    const int ly = row - r;
+    uint32_t w[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int lx = -8 + 32 * j + lane;
+      bool sd = false;
+      if (lx < TW + 8) {
+        const int c = XR6::idx(ly, lx);
+        sd = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
+      }
+      w[j] = __ballot_sync(0xffffffffu, sd);
+    }
+    if (lane == 0) {
+      // bit b of the row <-> column b - 8
+      const unsigned __int128 S = (unsigned __int128)w[0] | ((unsigned __int128)w[1] << 32) |
+                                  ((unsigned __int128)w[2] << 64);
+      uint64_t h = 0;
+      for (int d = -r; d <= r; ++d) h |= (uint64_t)(S >> (8 + d));  // column x + d for x = 0..63
+      hrow[row] = h;
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < H * TW; i += NT) {
-    const uint8_t* s = seed + (i / TW) * W + i % TW;  // columns lx-r .. lx+r
-    uint8_t v = 0;
-    for (int d = 0; d <= 2 * r; ++d) v |= s[d];
-    hor[i] = v;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < TH * TW; i += NT) {
-    const uint8_t* h = hor + i;  // rows ly-r .. ly+r
-    uint8_t v = 0;
-    for (int d = 0; d <= 2 * r; ++d) v |= h[d * TW];
-    sm.flags[i] = v ? 8 : 0;
+  {
+    const int ly = threadIdx.x / (TW / 8), g = threadIdx.x % (TW / 8);  // NT = TH * TW / 8 items
+    static_assert(NT == TH * TW / 8, "one 8-column group per thread");
+    uint64_t v = 0;
+    for (int d = 0; d <= 2 * r; ++d) v |= hrow[ly + d];
+    const uint32_t bits = (uint32_t)(v >> (8 * g)) & 0xffu;
+    // bit t -> byte t, value 8 (bit t moves to bit 8t by the multiply; no carries)
+    uint2 out;
+    out.x = (((bits & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
+    out.y = ((((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
+    *reinterpret_cast<uint2*>(sm.flags + ly * TW + 8 * g) = out;
   }
   __syncthreads();
 }
