@@ -525,7 +525,7 @@ struct QuadLoaderU16 {
 // (the original input >= satlevel at an unflagged pixel) of each row of the
 // tile + r as bits, by ballot over the staged columns -8..87 (those outside
 // -8..71 are not staged and hold no seed); the OR over columns -r..r by
-// shifts of the 128-bit row; then, per tile row and 8-column group, the OR
+// funnel shifts of adjacent words; then, per tile row and 8-column group, the OR
 // over rows -r..r expanded to flag bytes.  Out-of-frame positions hold
 // clamped copies, which add no seed an in-frame position does not hold
 // closer.  All threads; the list array is free scratch here.
@@ -549,14 +549,14 @@ __device__ __forceinline__ void sat_grown(const FrameDesc& f, SM& sm) {
       }
       w[j] = __ballot_sync(0xffffffffu, sd);
     }
-    if (lane == 0) {
-      // bit b of the row <-> column b - 8
-      const unsigned __int128 S = (unsigned __int128)w[0] | ((unsigned __int128)w[1] << 32) |
-                                  ((unsigned __int128)w[2] << 64);
-      uint64_t h = 0;
-      for (int d = -r; d <= r; ++d) h |= (uint64_t)(S >> (8 + d));  // column x + d for x = 0..63
-      hrow[row] = h;
+    // Bit b of w[] <-> column b - 8; output word j holds columns 32j..32j+31,
+    // and its OR over columns -r..r is an OR of funnel shifts by 8 + d.
+    uint32_t h0 = 0, h1 = 0;
+    for (int d = -r; d <= r; ++d) {
+      h0 |= __funnelshift_r(w[0], w[1], 8 + d);
+      h1 |= __funnelshift_r(w[1], w[2], 8 + d);
     }
+    if (lane == 0) hrow[row] = (uint64_t)h0 | ((uint64_t)h1 << 32);
   }
   __syncthreads();
   {
