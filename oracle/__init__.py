@@ -50,7 +50,7 @@ def _load():
             i, f, ll = ctypes.c_int, ctypes.c_float, ctypes.c_longlong
             for suf in ("f32", "f64"):
                 fn = getattr(lib, f"oracle_run_{suf}")
-                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, i, P, P, P, P]
+                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, i, i, P, P, P, P]
                 fn.restype = i
                 fn = getattr(lib, f"oracle_iterate_{suf}")
                 fn.argtypes = [P, P, i, i, f, f, f, f, f, i, P, P] + [P] * 12
@@ -59,9 +59,10 @@ def _load():
                     fn = getattr(lib, f"oracle_{name}_{suf}")
                     fn.argtypes = [P, i, i, P]
                     fn.restype = None
-                fn = getattr(lib, f"oracle_median_{suf}")
-                fn.argtypes = [P, i, i, i, P]
-                fn.restype = None
+                for name in ("median", "median_sep"):
+                    fn = getattr(lib, f"oracle_{name}_{suf}")
+                    fn.argtypes = [P, i, i, i, P]
+                    fn.restype = None
                 fn = getattr(lib, f"oracle_maskmed_{suf}")
                 fn.argtypes = [P, P, i, i, i, i, P]
                 fn.restype = i
@@ -83,9 +84,10 @@ def _dt(precision: str):
 
 def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 65535.0,
         sigclip: float = 4.5, sigfrac: float = 0.3, objlim: float = 5.0, niter: int = 4,
-        fnorm: bool = True, precision: str = "f32", satgrow: int = 0):
+        fnorm: bool = True, precision: str = "f32", satgrow: int = 0, sepmed: bool = False):
     """Full detect-and-clean loop.  Returns (mask u8, cleaned, iters_run, n_flagged).
-    satgrow: radius of the protected square around saturated pixels (reading C16)."""
+    satgrow: radius of the protected square around saturated pixels (reading C16).
+    sepmed: both 5x5 detection medians taken separably (comparison mode, reading C17)."""
     lib = _load()
     frame = np.ascontiguousarray(frame)
     if frame.dtype == np.uint16:
@@ -102,7 +104,7 @@ def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 6553
     nf = ctypes.c_longlong(0)
     rc = getattr(lib, f"oracle_run_{suf}")(
         _ptr(frame), dtype, ny, nx, gain, readnoise, satlevel, sigclip, sigfrac, objlim,
-        int(niter), int(bool(fnorm)), int(satgrow), _ptr(mask), _ptr(clean), ctypes.byref(it),
+        int(niter), int(bool(fnorm)), int(satgrow), int(bool(sepmed)), _ptr(mask), _ptr(clean), ctypes.byref(it),
         ctypes.byref(nf))
     if rc != 0:
         raise ValueError(f"oracle_run_{suf} failed with code {rc}")
@@ -155,6 +157,16 @@ def median(A: np.ndarray, K: int, precision: str = "f32"):
     A = np.ascontiguousarray(A, T)
     out = np.zeros_like(A)
     getattr(lib, f"oracle_median_{suf}")(_ptr(A), A.shape[0], A.shape[1], int(K), _ptr(out))
+    return out
+
+
+def median_sep(A: np.ndarray, K: int, precision: str = "f32"):
+    """Separable K x K median (median of the row medians), clamp-to-edge (C17)."""
+    lib = _load()
+    T, suf = _dt(precision)
+    A = np.ascontiguousarray(A, T)
+    out = np.zeros_like(A)
+    getattr(lib, f"oracle_median_sep_{suf}")(_ptr(A), A.shape[0], A.shape[1], int(K), _ptr(out))
     return out
 
 

@@ -108,6 +108,30 @@ void median_filter(const T* A, int ny, int nx, int K, T* out) {
   }
 }
 
+// Reading C17 (the comparison mode): the separable K x K median -- the
+// median over the K rows of the window of each row's K-tap median, with the
+// same clamped coordinates as median_filter.  The paper notes that
+// implementations using it for speed misclassify the centres of bright or
+// saturated stars as cosmic rays; this mode exists to show that, and is not
+// the method itself.
+template <class T>
+void median_filter_sep(const T* A, int ny, int nx, int K, T* out) {
+  const int r = K / 2;
+  std::vector<T> row((size_t)K), meds((size_t)K);
+  for (int i = 0; i < ny; ++i) {
+    for (int j = 0; j < nx; ++j) {
+      for (int di = -r; di <= r; ++di) {
+        for (int dj = -r; dj <= r; ++dj)
+          row[dj + r] = A[(size_t)clampi(i + di, 0, ny - 1) * nx + clampi(j + dj, 0, nx - 1)];
+        std::nth_element(row.begin(), row.begin() + r, row.end());
+        meds[di + r] = row[r];
+      }
+      std::nth_element(meds.begin(), meds.begin() + r, meds.end());
+      out[(size_t)i * nx + j] = meds[r];
+    }
+  }
+}
+
 // 3x3 binary dilation; out-of-frame positions count as false.
 void dilate3(const uint8_t* in, int ny, int nx, uint8_t* out) {
   for (int i = 0; i < ny; ++i)
@@ -152,6 +176,7 @@ struct Params {
   int niter;
   int fnorm;    // 1: F = max((m3-m7)/N, 0.01) (reading C6); 0: F = max(m3-m7, 0.01)
   int satgrow;  // reading C16: radius of the protected region around saturated pixels (0..4)
+  int sepmed;   // reading C17: 1 takes both 5x5 detection medians separably (comparison mode)
 };
 
 // Reading C16 (saturated-star protection, the paper's concern that centres
@@ -215,7 +240,7 @@ long long iterate(const T* X0, const uint8_t* sat, int ny, int nx, const Params<
   // Step 1: Laplacian detection (C1).
   lplus(I, ny, nx, L.data());
   // Step 2: noise model N = sqrt(max(g*med5(I), 1e-4) + rn^2) / g (C4), in ADU.
-  median_filter(I, ny, nx, 5, m5.data());
+  (p.sepmed ? median_filter_sep<T> : median_filter<T>)(I, ny, nx, 5, m5.data());
   for (size_t q = 0; q < n; ++q) {
     const T e = std::max(g * m5[q], T(1e-4));
     N[q] = std::sqrt(e + rn2) / g;
@@ -223,7 +248,7 @@ long long iterate(const T* X0, const uint8_t* sat, int ny, int nx, const Params<
   // Step 3: significance map S = L / (2N) (C5), then large-structure removal
   // S' = S - med5(S).
   for (size_t q = 0; q < n; ++q) S[q] = L[q] / (N[q] + N[q]);
-  median_filter(S.data(), ny, nx, 5, mS.data());
+  (p.sepmed ? median_filter_sep<T> : median_filter<T>)(S.data(), ny, nx, 5, mS.data());
   for (size_t q = 0; q < n; ++q) Sp[q] = S[q] - mS[q];
   // Step 5 input: fine-structure image F = max((med3(I) - med7(med3(I))) / N, 0.01) (C6).
   median_filter(I, ny, nx, 3, m3.data());
@@ -284,7 +309,7 @@ int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_
         T* clean_out, int* iters_run, long long* n_flagged) {
   if (!frame || ny < 1 || nx < 1 || (dtype != 0 && dtype != 1)) return -1;
   if (!params_ok(p.gain, p.readnoise, p.sigclip, p.sigfrac, p.objlim, p.niter)) return -1;
-  if (p.satgrow < 0 || p.satgrow > 4) return -1;
+  if (p.satgrow < 0 || p.satgrow > 4 || (p.sepmed != 0 && p.sepmed != 1)) return -1;
   const size_t n = (size_t)ny * nx;
   std::vector<T> X0;
   std::vector<uint8_t> sat;
@@ -317,11 +342,11 @@ int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_
 
 template <class T>
 Params<T> make_params(double gain, double rn, double satlevel, double sigclip, double sigfrac,
-                      double objlim, int niter, int fnorm, int satgrow) {
+                      double objlim, int niter, int fnorm, int satgrow, int sepmed) {
   Params<T> p;
   p.gain = (T)gain; p.readnoise = (T)rn; p.satlevel = (T)satlevel;
   p.sigclip = (T)sigclip; p.sigfrac = (T)sigfrac; p.objlim = (T)objlim;
-  p.niter = niter; p.fnorm = fnorm; p.satgrow = satgrow;
+  p.niter = niter; p.fnorm = fnorm; p.satgrow = satgrow; p.sepmed = sepmed;
   return p;
 }
 
@@ -336,19 +361,21 @@ extern "C" {
 
 int oracle_run_f32(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
-                   int fnorm, int satgrow, uint8_t* mask, float* clean, int* iters_run,
+                   int fnorm, int satgrow, int sepmed, uint8_t* mask, float* clean, int* iters_run,
                    long long* n_flagged) {
   return run<float>(frame, dtype, ny, nx,
-                    make_params<float>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow),
+                    make_params<float>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow,
+                                       sepmed),
                     mask, clean, iters_run, n_flagged);
 }
 
 int oracle_run_f64(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
-                   int fnorm, int satgrow, uint8_t* mask, double* clean, int* iters_run,
+                   int fnorm, int satgrow, int sepmed, uint8_t* mask, double* clean, int* iters_run,
                    long long* n_flagged) {
   return run<double>(frame, dtype, ny, nx,
-                     make_params<double>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow),
+                     make_params<double>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow,
+                                         sepmed),
                      mask, clean, iters_run, n_flagged);
 }
 
@@ -359,7 +386,7 @@ int oracle_run_f64(const void* frame, int dtype, int ny, int nx, float gain, flo
                                  float rn, float sigclip, float sigfrac, float objlim, int fnorm, \
                                  T* I, uint8_t* M, T* L, T* m5, T* N, T* S, T* mS, T* Sp, T* m3,  \
                                  T* m7, T* F, uint8_t* cand, uint8_t* g1, uint8_t* g2) {         \
-    Params<T> p = make_params<T>(gain, rn, 0.0, sigclip, sigfrac, objlim, 1, fnorm, 0);          \
+    Params<T> p = make_params<T>(gain, rn, 0.0, sigclip, sigfrac, objlim, 1, fnorm, 0, 0);       \
     Dumps<T> d{L, m5, N, S, mS, Sp, m3, m7, F, cand, g1, g2};                                     \
     return iterate<T>(X0, sat, ny, nx, p, I, M, &d);                                              \
   }
@@ -379,6 +406,12 @@ void oracle_median_f32(const float* A, int ny, int nx, int K, float* out) {
 }
 void oracle_median_f64(const double* A, int ny, int nx, int K, double* out) {
   median_filter(A, ny, nx, K, out);
+}
+void oracle_median_sep_f32(const float* A, int ny, int nx, int K, float* out) {
+  median_filter_sep(A, ny, nx, K, out);
+}
+void oracle_median_sep_f64(const double* A, int ny, int nx, int K, double* out) {
+  median_filter_sep(A, ny, nx, K, out);
 }
 void oracle_dilate3(const uint8_t* in, int ny, int nx, uint8_t* out) { dilate3(in, ny, nx, out); }
 void oracle_dilate_square(const uint8_t* in, int ny, int nx, int r, uint8_t* out) {

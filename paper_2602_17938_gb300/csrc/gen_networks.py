@@ -359,6 +359,38 @@ def block_median(K, W, R):
 
 
 BLOCKS = {"blk_med5_4x2": (5, 4, 2), "blk_med3_8x2": (3, 8, 2)}
+# Separable K x K medians (the median over K rows of each row's K-tap median):
+# the comparison mode of the detection medians.
+SEP_BLOCKS = {"blk_sep5_4x2": (5, 4, 2)}
+
+
+def _median_of(d, keys):
+    s = d.sort(list(keys))
+    return s[(len(keys) - 1) // 2]
+
+
+def sep_window_median(K):
+    """Separable K x K median of one window: K row medians, then their median."""
+    d = Dag()
+    v = [[d.inp((r, c)) for c in range(K)] for r in range(K)]
+    rows = [_median_of(d, v[r]) for r in range(K)]
+    return d, [_median_of(d, rows)]
+
+
+def sep_block_median(K, W, R):
+    """Separable K x K medians of a W-wide, R-tall block: each input row's
+    K-tap medians at the W output columns are formed once and shared by the
+    R output rows; then each output takes the median of its K row medians."""
+    d = Dag()
+    inp = [[d.inp((r, c)) for c in range(W + K - 1)] for r in range(R + K - 1)]
+    rm = [[_median_of(d, inp[r][c:c + K]) for c in range(W)] for r in range(R + K - 1)]
+    return d, [_median_of(d, [rm[y + a][x] for a in range(K)]) for y in range(R) for x in range(W)]
+
+
+def sep_reference(env, win_rows):
+    """Median over rows of the row medians, for a window given as rows of labels."""
+    meds = sorted(sorted(env[lab] for lab in row)[(len(row) - 1) // 2] for row in win_rows)
+    return meds[(len(meds) - 1) // 2]
 
 
 def build_all():
@@ -371,21 +403,41 @@ def build_all():
         nets[name] = (d, o, (R + K - 1, W + K - 1),
                       f"{K}x{K} medians of a {W}x{R} block (W x R); v is "
                       f"{R + K - 1}x{W + K - 1} row-major, o is {R}x{W} row-major.")
+    nets["sep5x5"] = sep_window_median(5) + ((5, 5), "Separable median of a 5x5 window (median of "
+                                                     "the row medians), v row-major.")
+    for name, (K, W, R) in SEP_BLOCKS.items():
+        d, o = sep_block_median(K, W, R)
+        nets[name] = (d, o, (R + K - 1, W + K - 1),
+                      f"Separable {K}x{K} medians of a {W}x{R} block (W x R); v is "
+                      f"{R + K - 1}x{W + K - 1} row-major, o is {R}x{W} row-major.")
     return nets
+
+
+def _window_rows(name, out_index):
+    """Rows of input labels of the window behind an output (separable networks)."""
+    if name in SEP_BLOCKS:
+        K, W, R = SEP_BLOCKS[name]
+        y, x = divmod(out_index, W)
+        return [[(y + a, x + b) for b in range(K)] for a in range(K)]
+    return [[(a, b) for b in range(5)] for a in range(5)]  # sep5x5
 
 
 def block_window(name, out_index):
     """Input labels (row, col) of the window behind output ``out_index`` of a block."""
-    K, W, R = BLOCKS[name]
+    K, W, R = BLOCKS[name] if name in BLOCKS else SEP_BLOCKS[name]
     y, x = divmod(out_index, W)
     return [(y + a, x + b) for a in range(K) for b in range(K)]
 
 
 def _windows(name, dag, outs):
     labels = [nm[1] for nm in dag.names if nm[0] == "in"]
-    if name in BLOCKS:
+    if name in BLOCKS or name in SEP_BLOCKS:
         return [block_window(name, j) for j in range(len(outs))]
     return [labels]
+
+
+def is_separable(name):
+    return name == "sep5x5" or name in SEP_BLOCKS
 
 
 def verify(nets=None, trials=2000, seed=1, exhaustive=True, max_exhaustive_outputs=None):
@@ -403,17 +455,26 @@ def verify(nets=None, trials=2000, seed=1, exhaustive=True, max_exhaustive_outpu
             env = {lab: rng.randint(0, hi) for lab in labels}
             got = evaluate(dag, outs, env)
             for j, win in enumerate(wins):
-                vals = sorted(env[lab] for lab in win)
-                if got[j] != vals[(len(vals) - 1) // 2]:
+                if is_separable(name):
+                    want = sep_reference(env, _window_rows(name, j))
+                else:
+                    vals = sorted(env[lab] for lab in win)
+                    want = vals[(len(vals) - 1) // 2]
+                if got[j] != want:
                     raise AssertionError(f"{name}: output {j} wrong on {env}")
         if exhaustive:
             for j, win in enumerate(wins[:max_exhaustive_outputs]):
                 if len(win) <= 25:
-                    _exhaustive01(dag, outs[j], win, labels)
+                    _exhaustive01(dag, outs[j], win, labels,
+                                  _window_rows(name, j) if is_separable(name) else None)
     return True
 
 
-def _exhaustive01(dag, out, win, labels):
+def _exhaustive01(dag, out, win, labels, rows=None):
+    """Every 0-1 assignment of the window; the reference is the median of the
+    window or, with ``rows``, the median of the row medians (both min/max
+    formulas, which by the 0-1 principle agree everywhere if they agree on
+    every 0-1 input)."""
     import numpy as np
     n = len(win)
     total = 1 << n
@@ -431,10 +492,15 @@ def _exhaustive01(dag, out, win, labels):
         if va is None or vb is None:
             raise AssertionError("output depends on an input outside its window")
         val[i] = (va & vb) if kind == "min" else (va | vb)
-    ones = np.zeros(total, dtype=np.int64)
-    for k in range(n):
-        ones += ((idx >> np.uint64(k)) & np.uint64(1)).astype(np.int64)
-    expect = ones >= (n + 1) // 2  # the median of n (odd) 0/1 keys is 1 iff #ones > n/2
+    def bit(k):
+        return ((idx >> np.uint64(k)) & np.uint64(1)).astype(np.int64)
+
+    if rows is None:
+        ones = sum(bit(k) for k in range(n))
+        expect = ones >= (n + 1) // 2  # the median of n (odd) 0/1 keys is 1 iff #ones > n/2
+    else:
+        row_meds = [sum(bit(inwin[lab]) for lab in row) >= (len(row) + 1) // 2 for row in rows]
+        expect = sum(m.astype(np.int64) for m in row_meds) >= (len(rows) + 1) // 2
     got = val[out] if isinstance(out, int) else np.full(total, out == POS)
     if not np.array_equal(np.asarray(got, dtype=bool), expect):
         raise AssertionError("0-1 exhaustive check failed")
@@ -448,7 +514,7 @@ HEADER = """// Generated by gen_networks.py -- do not edit.
 
 
 # Networks also emitted in the fetch-at-first-use form.
-LOADER_NETS = ("blk_med5_4x2", "blk_med3_8x2", "med5x5", "med7x7")
+LOADER_NETS = ("blk_med5_4x2", "blk_med3_8x2", "med5x5", "med7x7", "sep5x5", "blk_sep5_4x2")
 
 
 def main(out_path):

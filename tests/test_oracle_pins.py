@@ -340,6 +340,50 @@ def test_satgrow_protects_a_hit_next_to_a_saturated_core():
     assert m3[41, 45] == 0
 
 
+def _sep_median_numpy(A, K):
+    r = K // 2
+    P = np.pad(A, r, mode="edge")
+    # row medians over columns j-r..j+r of every padded row, then medians over rows i-r..i+r
+    rm = np.median(sliding_window_view(P, K, axis=1), axis=-1)  # (ny + 2r) x nx
+    return np.median(sliding_window_view(rm, K, axis=0), axis=-1)
+
+
+@pytest.mark.parametrize("K", [3, 5])
+def test_separable_median_matches_numpy(K):
+    # Reading C17: an independent numpy form (edge padding = clamped coordinates).
+    rng = np.random.default_rng(60 + K)
+    for shape in [(1, 1), (1, 7), (6, 1), (9, 13), (40, 33)]:
+        A = rng.integers(0, 50, shape).astype(np.float32)  # many ties
+        assert np.array_equal(oracle.median_sep(A, K), _sep_median_numpy(A, K).astype(np.float32)), shape
+
+
+def test_separable_median_equals_true_median_on_row_constant_images():
+    # A window of an image constant along each row holds each row value K times,
+    # so the true median is the median of the row values -- the separable one.
+    rng = np.random.default_rng(71)
+    a = rng.normal(100, 20, 37).astype(np.float32)
+    A = np.repeat(a[:, None], 29, axis=1)
+    assert np.array_equal(oracle.median_sep(A, 5), oracle.median(A, 5))
+    # and it differs from the true median on a generic image
+    B = rng.normal(100, 20, (37, 29)).astype(np.float32)
+    assert not np.array_equal(oracle.median_sep(B, 5), oracle.median(B, 5))
+
+
+def test_sepmed_mode_changes_the_mask_on_star_fields():
+    # The comparison mode swaps only the two 5x5 detection medians; on a field
+    # of bright Gaussian stars (flat tops clipped at 65535) the two modes give
+    # different masks.  (Which one flags more depends on the data: on these
+    # synthetic stars the separable mode flags fewer star pixels.)
+    from paper_2602_17938_gb300 import synth
+    spec = synth.FrameSpec(256, 256, "f32", (17, 3), sky=300.0, gain=1.0, readnoise=3.0,
+                           n_stars=40, star_peak=(1e5, 1e6), n_tracks=0, hot_frac=0.0, fwhm=3.5)
+    f = np.minimum(synth.make_frame(spec), 65535.0).astype(np.float32)
+    m_true, _, _, n_true = oracle.run(f, 1.0, 3.0, satlevel=65535.0)
+    m_sep, _, _, n_sep = oracle.run(f, 1.0, 3.0, satlevel=65535.0, sepmed=True)
+    assert n_true > 0 and n_sep > 0 and not np.array_equal(m_true, m_sep)
+    assert not (m_sep.astype(bool) & (f >= 65535.0)).any()  # saturated pixels stay protected
+
+
 def _config0():
     from paper_2602_17938_gb300 import synth
     spec = synth.config_specs(0)[0]
