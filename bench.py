@@ -348,7 +348,7 @@ def run_ours(args):
 
     # Optional modes on the same frame, timed the same way (device, L2 flushed).
     modes = {}
-    for name, extra in (("default", dict()), ("satgrow2", dict(satgrow=2))):
+    for name, extra in (("default", dict()), ("satgrow2", dict(satgrow=2)), ("sepmed", dict(sepmed=True))):
         mp = lacos.make_params(spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac,
                                spec.objlim, spec.niter, True, **extra)
         for _ in range(2):

@@ -70,12 +70,16 @@ enum {
  * satgrow: 0..4, saturated-star protection: the pixels within this many
  * pixels (Chebyshev distance) of a saturated input pixel are treated as
  * saturated too (never flagged, never replaced); 0 protects only the
- * saturated pixels themselves. */
+ * saturated pixels themselves.
+ * sepmed: 0 (the method), or 1 for the comparison mode that takes both 5x5
+ * detection medians (noise model, large-structure removal) separably: the
+ * median of the five row medians, as faster implementations do. */
 typedef struct {
   float gain, readnoise, satlevel, sigclip, sigfrac, objlim;
   int niter;
   int fine_norm;
   int satgrow;
+  int sepmed;
 } lacos_params;
 
 typedef struct {

@@ -164,6 +164,7 @@ static bool params_valid(const lacos_params* p) {
   if (p->niter < 0 || p->niter > LACOS_MAX_NITER) return false;
   if (p->fine_norm != 0 && p->fine_norm != 1) return false;
   if (p->satgrow < 0 || p->satgrow > 4) return false;
+  if (p->sepmed != 0 && p->sepmed != 1) return false;
   return true;
 }
 
@@ -250,6 +251,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.niter = f.p.niter;
     h.fnorm = f.p.fine_norm;
     h.satgrow = f.p.satgrow;
+    h.sepmed = f.p.sepmed;
     h.tiles_x = (f.nx + TW - 1) / TW;
     const unsigned tiles = (unsigned)h.tiles_x * (unsigned)((f.ny + TH - 1) / TH);
     h.tile_begin = total;
@@ -803,6 +805,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.niter = p->niter;
   h.fnorm = p->fine_norm;
   h.satgrow = p->satgrow;
+  h.sepmed = p->sepmed;
   h.tiles_x = (nx + TW - 1) / TW;
   const unsigned total = (unsigned)h.tiles_x * (unsigned)((ny + TH - 1) / TH);
   h.tile_begin = 0;

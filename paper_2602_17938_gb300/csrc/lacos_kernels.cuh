@@ -104,6 +104,7 @@ struct FrameDesc {
   float gain, rn2, satlevel, sigclip, lo, thr_min, objlim;
   int niter, fnorm;
   int satgrow;       // radius of the protected region around saturated pixels (0..4)
+  int sepmed;        // 1: both 5x5 detection medians taken separably (comparison mode)
   int tiles_x;
   unsigned int tile_begin, tile_end;    // this frame's range in the flattened tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
@@ -652,7 +653,10 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
       constexpr int P = S_BW + 4;
       const QuadLoaderF32<P> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       float m5[S_BH * S_BW];
-      blk_med5_4x2_ld<float>(ld, m5);
+      if (f.sepmed)
+        blk_sep5_4x2_ld<float>(ld, m5);
+      else
+        blk_med5_4x2_ld<float>(ld, m5);
       // med5 parked in S; dense_pixels turns it into N and S.
 #pragma unroll
       for (int r = 0; r < S_BH; ++r)
@@ -697,7 +701,10 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
       constexpr int P = S_BW + 4;
       const QuadLoaderU16<P, S_DY> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       U16x2 m5[S_BH * S_BW];
-      blk_med5_4x2_ld<U16x2>(ld, m5);
+      if (f.sepmed)
+        blk_sep5_4x2_ld<U16x2>(ld, m5);
+      else
+        blk_med5_4x2_ld<U16x2>(ld, m5);
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -964,7 +971,10 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     const float* wb = sm.S + c - 2 * Reg<2>::W - 2;
     const auto ld5 = [&](int e) { return wb[(e / 5) * Reg<2>::W + e % 5]; };
     float m;
-    med5x5_ld<float>(ld5, &m);
+    if (f.sepmed)
+      sep5x5_ld<float>(ld5, &m);
+    else
+      med5x5_ld<float>(ld5, &m);
     const float sp = __fsub_rn(sm.S[c], m);
     const bool sat = (sm.flags[i] & 8) != 0;  // never set for fine items
     const uint32_t bit = 1u << (lx & 31);

@@ -34,7 +34,8 @@ class Params(ctypes.Structure):
     _fields_ = [("gain", ctypes.c_float), ("readnoise", ctypes.c_float),
                 ("satlevel", ctypes.c_float), ("sigclip", ctypes.c_float),
                 ("sigfrac", ctypes.c_float), ("objlim", ctypes.c_float),
-                ("niter", ctypes.c_int), ("fine_norm", ctypes.c_int), ("satgrow", ctypes.c_int)]
+                ("niter", ctypes.c_int), ("fine_norm", ctypes.c_int), ("satgrow", ctypes.c_int),
+                ("sepmed", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -53,9 +54,9 @@ class Result(ctypes.Structure):
 
 
 def make_params(gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0.3, objlim=5.0,
-                niter=4, fine_norm=True, satgrow=0) -> Params:
+                niter=4, fine_norm=True, satgrow=0, sepmed=False) -> Params:
     return Params(gain, readnoise, satlevel, sigclip, sigfrac, objlim, int(niter), int(bool(fine_norm)),
-                  int(satgrow))
+                  int(satgrow), int(bool(sepmed)))
 
 
 _lib = None
@@ -275,7 +276,8 @@ class Context:
 
 
 def clean_frame(frame, gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0.3, objlim=5.0,
-                niter=4, fine_norm=True, ctx: Context | None = None, stream=None, satgrow=0):
+                niter=4, fine_norm=True, ctx: Context | None = None, stream=None, satgrow=0,
+                sepmed=False):
     """Detect and clean one device frame; returns (mask uint8, cleaned float32, FrameResult)."""
     import torch
     own = ctx is None
@@ -283,7 +285,8 @@ def clean_frame(frame, gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0
     try:
         mask = torch.empty(frame.shape, dtype=torch.uint8, device=frame.device)
         clean = torch.empty(frame.shape, dtype=torch.float32, device=frame.device)
-        p = make_params(gain, readnoise, satlevel, sigclip, sigfrac, objlim, niter, fine_norm, satgrow)
+        p = make_params(gain, readnoise, satlevel, sigclip, sigfrac, objlim, niter, fine_norm, satgrow,
+                        sepmed)
         t = ctx.submit(frame, p, mask, clean, stream)
         res = ctx.wait(t)
         return mask, clean, res

@@ -143,6 +143,21 @@ def test_saturated_star_protection(ctx, r, dtype):
     assert (m0.astype(int) - m_ref.astype(int)).max() == 1, "the protection should remove some flags"
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.uint16])
+def test_separable_median_mode(ctx, dtype):
+    # The comparison mode (both 5x5 detection medians separable) against the
+    # oracle's separable median, bit for bit: hits on noise plus bright stars.
+    from paper_2602_17938_gb300 import synth
+    for seed, shape in ((3, (200, 333)), (8, (129, 64))):
+        spec = synth.FrameSpec(*shape, "f32", (30, seed), sky=300.0, gain=1.0, readnoise=3.0,
+                               n_stars=12, star_peak=(1e4, 4e5), n_tracks=60, hot_frac=0.002, fwhm=3.0)
+        f = np.minimum(synth.make_frame(spec), 65535.0)
+        frame = np.rint(f).astype(np.uint16) if dtype == np.uint16 else f.astype(np.float32)
+        m_ref, _ = assert_same(frame, 1.0, 3.0, gpu_run(ctx, frame, 1.0, 3.0, sepmed=True), sepmed=True)
+        m_true, *_ = oracle.run(frame, 1.0, 3.0)
+        assert not np.array_equal(m_ref, m_true)
+
+
 def test_varied_parameters(ctx):
     f = noisy_with_hits(140, 160, seed=8)
     for kw in ({"sigclip": 3.0, "sigfrac": 0.5, "objlim": 2.0}, {"sigclip": 6.0, "sigfrac": 1.5, "objlim": 8.0},
@@ -170,6 +185,11 @@ def test_argument_errors(ctx):
         with pytest.raises(lacos.LacosError) as e:
             ctx.submit(f, lacos.make_params(**kw), m, c)
         assert e.value.code == lacos.EINVAL
+    p = lacos.make_params(1.0, 1.5)
+    p.sepmed = 2  # only 0 or 1
+    with pytest.raises(lacos.LacosError) as e:
+        ctx.submit(f, p, m, c)
+    assert e.value.code == lacos.EINVAL
     with pytest.raises(lacos.LacosError) as e:
         ctx.poll(123456789)
     assert e.value.code == lacos.EUNKNOWN_TICKET
