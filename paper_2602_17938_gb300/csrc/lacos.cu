@@ -110,7 +110,8 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
   size_t off = L.masks;
   for (const auto& f : fr) {
     L.mask_off.push_back(off);
-    off += 5 * maskbuf_bytes(f.ny, f.nx) + kNtabBytes + tflag_bytes(f.ny, f.nx);  // M 0/1, sig/lo/cand, N table, tile marks
+    // M 0/1, sig/lo/cand, N table, tile marks, and with satgrow the grown saturated set
+    off += (f.p.satgrow ? 6 : 5) * maskbuf_bytes(f.ny, f.nx) + kNtabBytes + tflag_bytes(f.ny, f.nx);
   }
   L.total = off;
   return L;
@@ -235,6 +236,8 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.p_cand = (uint32_t*)(d + L.mask_off[i] + 4 * mb);
     h.ntab = (float2*)(d + L.mask_off[i] + 5 * mb);
     h.tflags = (uint8_t*)(d + L.mask_off[i] + 5 * mb + kNtabBytes);
+    h.p_sat = f.p.satgrow ? (uint32_t*)(d + L.mask_off[i] + 5 * mb + kNtabBytes + tflag_bytes(f.ny, f.nx))
+                          : nullptr;
     h.mask_out = f.mask;
     h.clean_out = f.clean;
     h.st = dstate + i;
@@ -298,6 +301,13 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     return LACOS_OK;
   };
   ntab_kernel<<<dim3(256, nf), 256, 0, s>>>(ddesc, nf);
+  for (size_t j = 0; j < fr.size(); ++j) {  // the grown saturated sets (C16)
+    const FrameReq& f = fr[order[j]];
+    if (!f.p.satgrow) continue;
+    const unsigned nw = (unsigned)((size_t)f.ny * wpr_of(f.nx));
+    satseed_kernel<<<(nw + 255) / 256, 256, 0, s>>>(ddesc, (int)j, nw);
+    satgrow_kernel<<<(nw + 255) / 256, 256, 0, s>>>(ddesc, (int)j, nw);
+  }
   CK(cudaGetLastError());
   for (int k = 1; k <= max_niter; ++k) {
     for (int dt : {1, 0}) {
@@ -762,7 +772,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const size_t off_desc = align_up(sizeof(unsigned) * kHeads);
   const size_t off_state = off_desc + align_up(sizeof(FrameDesc));
   const size_t off_masks = off_state + align_up(sizeof(FrameState));
-  const size_t need = off_masks + 5 * mb + kNtabBytes + tflag_bytes(ny, nx);
+  const size_t need = off_masks + (p->satgrow ? 6 : 5) * mb + kNtabBytes + tflag_bytes(ny, nx);
   if (need > (size_t)LACOS_STATIC_SCRATCH_BYTES) return LACOS_ENOMEM;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LACOS_ECUDA;
@@ -789,6 +799,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.p_cand = (uint32_t*)(planes + 4 * mb);
   h.ntab = (float2*)(planes + 5 * mb);
   h.tflags = (uint8_t*)(planes + 5 * mb + kNtabBytes);
+  h.p_sat = p->satgrow ? (uint32_t*)(planes + 5 * mb + kNtabBytes + tflag_bytes(ny, nx)) : nullptr;
   h.mask_out = d_mask;
   h.clean_out = d_clean;
   h.st = dstate;
@@ -828,6 +839,11 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core[di]));
   const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
+  if (p->satgrow) {
+    const unsigned nw = (unsigned)((size_t)ny * wpr_of(nx));
+    satseed_kernel<<<(nw + 255) / 256, 256, 0, s>>>(ddesc, 0, nw);
+    satgrow_kernel<<<(nw + 255) / 256, 256, 0, s>>>(ddesc, 0, nw);
+  }
   for (int k = 1; k <= p->niter; ++k) {
     kCoreVariants[di][sd->core_variant]<<<gd, NT, kCoreSmem[di], s>>>(ddesc, 1, 0, total, k,
                                                                       heads + kHeadCore + di * kHeadLevels + k);

@@ -98,6 +98,7 @@ struct FrameDesc {
   uint32_t* p_cand;
   float2* ntab;      // uint16 frames: {2N, RN(1/(2N))} for every integer med5 value 0..65535
   uint8_t* tflags;   // per core tile: [2][tiles] "recompute at level k" (buffer k & 1), [tiles] sticky
+  uint32_t* p_sat;   // satgrow > 0: the grown saturated set (C16) as 32-pixel words, built per request
   uint8_t* mask_out;
   float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
@@ -392,6 +393,61 @@ __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
   if (f.dtype == 1) f.ntab[m] = ntab_entry(f, m);
 }
 
+// Saturated-star protection (C16), once per request: the seeds (input >=
+// satlevel; a saturated pixel is never flagged, so the set does not depend
+// on the mask) as 32-pixel words, staged in the level-1 mask buffer, which
+// nothing reads before the first growth pass writes it ...
+__global__ void satseed_kernel(const FrameDesc* __restrict__ fr, int fi, unsigned nwords) {
+  // A warp forms 32 consecutive words, one per step: lane l tests pixel l of
+  // the word (contiguous loads), the ballot is the word, lane j keeps word j.
+  const FrameDesc& f = fr[fi];
+  const unsigned base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  const int lane = threadIdx.x & 31;
+  uint32_t mine = 0;
+  float v[32];  // all 32 loads in flight before the ballots
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const unsigned q = base + j;
+    v[j] = -1.0f;
+    if (q < nwords) {
+      const int y = (int)(q / (unsigned)f.wpr), x = (int)(q % (unsigned)f.wpr) * 32 + lane;
+      if (x < f.nx) {
+        const size_t p = (size_t)y * f.nx + x;
+        v[j] = f.dtype == 1 ? (float)__ldg((const unsigned short*)f.x0 + p) : __ldg((const float*)f.x0 + p);
+      }
+    }
+  }
+  const bool on = f.satlevel > 0.0f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t word = __ballot_sync(0xffffffffu, on && v[j] >= f.satlevel);
+    if (lane == j) mine = word;
+  }
+  if (base + lane < nwords) f.mbuf1[base + lane] = mine;
+}
+
+// ... then grown by the square of radius satgrow: per word, the OR over rows
+// -r..r of each row's OR over columns -r..r (funnel shifts with the
+// neighbouring words; bits beyond the frame are never set).
+__global__ void satgrow_kernel(const FrameDesc* __restrict__ fr, int fi, unsigned nwords) {
+  const FrameDesc& f = fr[fi];
+  const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nwords) return;
+  const int y = (int)(q / (unsigned)f.wpr), w = (int)(q % (unsigned)f.wpr), r = f.satgrow;
+  uint32_t g = 0;
+#pragma unroll
+  for (int a = -4; a <= 4; ++a) {  // rows -r..r (r <= 4), all loads in flight
+    const int yy = y + a;
+    if (a < -r || a > r || yy < 0 || yy >= f.ny) continue;
+    const uint32_t* row = f.mbuf1 + (size_t)yy * f.wpr;
+    const uint32_t c = row[w], lft = w > 0 ? row[w - 1] : 0u, rgt = w + 1 < f.wpr ? row[w + 1] : 0u;
+    uint32_t h = c;
+    for (int d = 1; d <= r; ++d) h |= __funnelshift_r(c, rgt, d) | __funnelshift_l(lft, c, d);
+    g |= h;
+  }
+  f.p_sat[q] = g;
+}
+
 // L / D rounded to nearest, for D > 0, L >= 0 and y = RN(1/D), without a
 // divide: Markstein's correction (P. Markstein, "Computation of elementary
 // functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34(1),
@@ -450,6 +506,7 @@ template <> struct CoreSmemT<float> {
                                  // items from the front and S'-only items from the back
   uint8_t flags[TH * TW];        // bit3: saturated
   uint32_t pw[3][TH][TWW];       // the tile's sig, lo and candidate bit-plane words
+  uint32_t Sw[TH][TWW];          // satgrow > 0: the tile's words of the grown saturated set
   unsigned nlist, nlist2;        // list lengths (S'-only, fine-structure)
   unsigned nfine;                // F evaluations of the tile
 };
@@ -463,6 +520,7 @@ template <> struct CoreSmemT<uint16_t> {
   uint16_t list[Reg<4>::N];
   uint8_t flags[TH * TW];
   uint32_t pw[3][TH][TWW];
+  uint32_t Sw[TH][TWW];
   unsigned nlist, nlist2;
   unsigned nfine;
 };
@@ -522,59 +580,6 @@ struct QuadLoaderU16 {
   }
 };
 
-// Saturation flags with protection radius r = satgrow > 0 (1..4): the seeds
-// (the original input >= satlevel at an unflagged pixel) of each row of the
-// tile + r as bits, by ballot over the staged columns -8..87 (those outside
-// -8..71 are not staged and hold no seed); the OR over columns -r..r by
-// funnel shifts of adjacent words; then, per tile row and 8-column group, the OR
-// over rows -r..r expanded to flag bytes.  Out-of-frame positions hold
-// clamped copies, which add no seed an in-frame position does not hold
-// closer.  All threads; the list array is free scratch here.
-template <class XT, class SM>
-__device__ __forceinline__ void sat_grown(const FrameDesc& f, SM& sm) {
-  const int r = f.satgrow;
-  uint64_t* hrow = reinterpret_cast<uint64_t*>(sm.list);  // rows -r .. TH+r-1: bit x = column x
-  static_assert((TH + 8) * sizeof(uint64_t) <= sizeof(sm.list) && TW == 64, "satgrow scratch");
-  const bool chk = f.satlevel > 0.0f;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int row = warp; row < TH + 2 * r; row += NT / 32) {
-    const int ly = row - r;
-    uint32_t w[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int lx = -8 + 32 * j + lane;
-      bool sd = false;
-      if (lx < TW + 8) {
-        const int c = XR6::idx(ly, lx);
-        sd = chk && !sm.Mb[c] && (float)sm.X[c] >= f.satlevel;
-      }
-      w[j] = __ballot_sync(0xffffffffu, sd);
-    }
-    // Bit b of w[] <-> column b - 8; output word j holds columns 32j..32j+31,
-    // and its OR over columns -r..r is an OR of funnel shifts by 8 + d.
-    uint32_t h0 = 0, h1 = 0;
-    for (int d = -r; d <= r; ++d) {
-      h0 |= __funnelshift_r(w[0], w[1], 8 + d);
-      h1 |= __funnelshift_r(w[1], w[2], 8 + d);
-    }
-    if (lane == 0) hrow[row] = (uint64_t)h0 | ((uint64_t)h1 << 32);
-  }
-  __syncthreads();
-  {
-    const int ly = threadIdx.x / (TW / 8), g = threadIdx.x % (TW / 8);  // NT = TH * TW / 8 items
-    static_assert(NT == TH * TW / 8, "one 8-column group per thread");
-    uint64_t v = 0;
-    for (int d = 0; d <= 2 * r; ++d) v |= hrow[ly + d];
-    const uint32_t bits = (uint32_t)(v >> (8 * g)) & 0xffu;
-    // bit t -> byte t, value 8 (bit t moves to bit 8t by the multiply; no carries)
-    uint2 out;
-    out.x = (((bits & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
-    out.y = ((((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
-    *reinterpret_cast<uint2*>(sm.flags + ly * TW + 8 * g) = out;
-  }
-  __syncthreads();
-}
-
 // Assignment of the dense step's block units to (round, thread): the med5
 // units first, the med3 units after them starting at a warp boundary, so
 // that no warp runs both kinds (a warp with both would execute the two
@@ -607,7 +612,18 @@ __device__ __forceinline__ void sat_flags(const FrameDesc& f, SM& sm) {
   static_assert(FIRST >= 0 && FIRST < NT, "some threads must take the flags");
   constexpr int first = FIRST;
   const int tid = (int)threadIdx.x;
-  if (f.satgrow) return;  // the grown region is formed after the networks (sat_grown)
+  if (f.satgrow) {  // the grown set (C16), built once per request: expand the tile's words
+    for (int q = tid - first; q < TH * TW / 8; q += NT - first) {
+      const int ly = q / (TW / 8), g = q % (TW / 8);
+      const uint32_t bits = (sm.Sw[ly][g >> 2] >> (8 * (g & 3))) & 0xffu;
+      // bit t -> byte t, value 8 (bit t moves to bit 8t by the multiply; no carries)
+      uint2 out;
+      out.x = (((bits & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
+      out.y = ((((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u) << 3;
+      *reinterpret_cast<uint2*>(sm.flags + ly * TW + 8 * g) = out;
+    }
+    return;
+  }
   if (tid < first) return;
   const bool chk = f.satlevel > 0.0f;
   for (int q = tid - first; q < TH * TW / 4; q += NT - first) {
@@ -866,9 +882,19 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
   for (int i = tid; i < 3 * TH * TWW; i += NT) (&sm.pw[0][0][0])[i] = 0u;
   if (tid == 0) sm.nfine = 0;
 
+  // The tile's words of the grown saturated set (satgrow > 0): the load is
+  // issued before the staging and stored after it, so it waits for nothing.
+  const bool sat_words = f.satgrow && tid < TH * TWW;
+  uint32_t sw = 0;
+  if (sat_words) {
+    const int ly = tid / TWW, w = (ox >> 5) + tid % TWW;
+    if (w < f.wpr) sw = __ldg(f.p_sat + (size_t)min(oy + ly, ny - 1) * f.wpr + w);
+  }
+
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
   bool bad = false;
   stage_x0_mask<6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
+  if (sat_words) sm.Sw[tid / TWW][tid % TWW] = sw;
   if (tid == 0) sm.nlist = 0;
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
@@ -936,7 +962,6 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     dense_f32(f, sm);
   if (tid == 0) sm.nlist2 = 0;
   __syncthreads();
-  if (f.satgrow) sat_grown<XT>(f, sm);
   dense_pixels(f, sm, oy, ox);
   __syncthreads();
   if (edge) {
