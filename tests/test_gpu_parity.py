@@ -238,6 +238,37 @@ def test_batch_equals_single_frames(ctx):
         assert agg.n_flagged == sum(p.n_flagged for p in per)
 
 
+def test_batch_mixes_modes_per_frame(ctx):
+    # One batched request whose frames use different modes (protection radius,
+    # separable medians, dtypes): each frame equals the oracle with its own
+    # parameters, through the graph-captured and replayed launches too.
+    from paper_2602_17938_gb300 import lacos
+    rng = np.random.default_rng(55)
+    frames = []
+    for i, (shape, dt) in enumerate([((90, 130), np.float32), ((70, 200), np.uint16),
+                                      ((129, 64), np.uint16), ((40, 40), np.float32)]):
+        f = noisy_with_hits(*shape, seed=60 + i).astype(np.float64)
+        for _ in range(3):  # saturated cores with hits nearby
+            y, x = int(rng.integers(2, shape[0] - 3)), int(rng.integers(2, shape[1] - 3))
+            f[y - 1:y + 2, x - 1:x + 2] = 65535.0
+            f[min(y + 3, shape[0] - 1), x] += 2000.0
+        frames.append(np.clip(np.rint(f), 0, 65535).astype(np.uint16) if dt == np.uint16 else f.astype(np.float32))
+    modes = [dict(satgrow=2), dict(sepmed=True), dict(satgrow=4, sepmed=True), dict()]
+    dev = [lacos.to_device(x) for x in frames]
+    masks = [torch.empty(x.shape, dtype=torch.uint8, device="cuda") for x in frames]
+    cleans = [torch.empty(x.shape, dtype=torch.float32, device="cuda") for x in frames]
+    ps = [lacos.make_params(1.0, 1.5, niter=5, **m) for m in modes]
+    for reuse in (False, True, True):
+        t, per = ctx.submit_batch(dev, ps, masks, cleans, reuse_graph=reuse)
+        ctx.wait(t)
+        torch.cuda.synchronize()
+        for i, x in enumerate(frames):
+            m_ref, c_ref, it_ref, nf_ref = oracle.run(x, 1.0, 1.5, niter=5, **modes[i])
+            assert np.array_equal(masks[i].cpu().numpy(), m_ref), i
+            assert np.array_equal(cleans[i].cpu().numpy().view(np.uint32), c_ref.view(np.uint32)), i
+            assert per[i].iters_run == it_ref and per[i].n_flagged == nf_ref
+
+
 def _crop_check(frame, spec, mask, clean, boxes, margin=64):
     ny, nx = frame.shape
     for (y0, y1, x0, x1) in boxes:
