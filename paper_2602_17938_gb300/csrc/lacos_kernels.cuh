@@ -398,10 +398,45 @@ __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
 // on the mask) as 32-pixel words, staged in the level-1 mask buffer, which
 // nothing reads before the first growth pass writes it ...
 __global__ void satseed_kernel(const FrameDesc* __restrict__ fr, int fi, unsigned nwords) {
-  // A warp forms 32 consecutive words, one per step: lane l tests pixel l of
-  // the word (contiguous loads), the ballot is the word, lane j keeps word j.
   const FrameDesc& f = fr[fi];
-  const unsigned base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  const unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = f.satlevel > 0.0f;
+  const int V = f.dtype == 1 ? 8 : 4;  // pixels per 16-byte load
+  if ((reinterpret_cast<uintptr_t>(f.x0) & 15u) == 0 && f.nx % V == 0) {
+    // Every row starts on a 16-byte boundary and holds whole 16-byte chunks:
+    // one thread per word, 16-byte loads of its chunks (a row's last word may
+    // hold fewer than 32 pixels).
+    if (q0 >= nwords) return;
+    const int y = (int)(q0 / (unsigned)f.wpr), x0 = (int)(q0 % (unsigned)f.wpr) * 32;
+    const int nch = min(32, f.nx - x0) / V;
+    const size_t p0 = (size_t)y * f.nx + x0;
+    uint32_t bits = 0;
+    if (on) {
+      if (f.dtype == 1) {
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(f.x0) + p0);
+        for (int c = 0; c < nch; ++c) {
+          const uint4 u = __ldg(src + c);
+          const uint32_t h[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            bits |= ((float)((h[e >> 1] >> (16 * (e & 1))) & 0xffffu) >= f.satlevel ? 1u : 0u) << (8 * c + e);
+        }
+      } else {
+        const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(f.x0) + p0);
+        for (int c = 0; c < nch; ++c) {
+          const float4 u = __ldg(src + c);
+          const float e4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) bits |= (e4[e] >= f.satlevel ? 1u : 0u) << (4 * c + e);
+        }
+      }
+    }
+    f.mbuf1[q0] = bits;
+    return;
+  }
+  // General layout: a warp forms 32 consecutive words, one per step (lane l
+  // tests pixel l of the word; the ballot is the word; lane j keeps word j).
+  const unsigned base = q0 & ~31u;
   const int lane = threadIdx.x & 31;
   uint32_t mine = 0;
   float v[32];  // all 32 loads in flight before the ballots
@@ -417,7 +452,6 @@ __global__ void satseed_kernel(const FrameDesc* __restrict__ fr, int fi, unsigne
       }
     }
   }
-  const bool on = f.satlevel > 0.0f;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const uint32_t word = __ballot_sync(0xffffffffu, on && v[j] >= f.satlevel);
