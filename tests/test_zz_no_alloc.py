@@ -36,11 +36,14 @@ def test_static_entry_point_matches_submit_twice():
         pytest.skip("no CUDA device")
     from paper_2602_17938_gb300 import build, lacos
     build.build()
-    cases = [(_frame(700, 901, 1), 1.0, 4), (_frame(513, 640, 2, np.uint16), 0.8, 6)]
+    sat = _frame(300, 400, 3, np.uint16)
+    sat[100:103, 200:203] = 65535  # a saturated core for the protection mode
+    cases = [(_frame(700, 901, 1), 1.0, 4, {}), (_frame(513, 640, 2, np.uint16), 0.8, 6, {}),
+             (sat, 1.0, 4, dict(satgrow=3)), (_frame(256, 320, 4), 1.2, 4, dict(sepmed=True))]
     with lacos.Context(0) as ctx:
-        for frame, gain, niter in cases:
+        for frame, gain, niter, mode in cases:
             d = lacos.to_device(frame)
-            p = lacos.make_params(gain, 1.5, niter=niter)
+            p = lacos.make_params(gain, 1.5, niter=niter, **mode)
             m_ref = torch.empty(frame.shape, dtype=torch.uint8, device="cuda")
             c_ref = torch.empty(frame.shape, dtype=torch.float32, device="cuda")
             r_ref = ctx.wait(ctx.submit(d, p, m_ref, c_ref))
