@@ -8,6 +8,8 @@
   subset -- every 8th of the 256 frames, all three niter values -- in one
   batched request.
 
+* The largest frame the ABI accepts (46340 x 46340 uint16, 2.1e9 pixels).
+
 Outputs are compared bit for bit with the float32 oracle on sampled boxes
 (the oracle runs a crop with a 64-pixel margin, more than six iterations
 can reach), and every frame satisfies the any-size properties: cleaned
@@ -115,3 +117,38 @@ def test_stress_subset_one_batched_launch(lacos):
             checked.add(sp.niter)
             _check(f, sp, m, c, _boxes(f, rng, sat_box=True))
     assert checked == {1, 4, 6}
+
+
+def test_largest_frame_sampled(lacos):
+    # The largest frame the ABI accepts (ny * nx < 2^31): 46340 x 46340 uint16, about 16 GB
+    # on the device with the outputs and scratch.  Drawn on the device (sky, read noise,
+    # hits), then checked against the oracle on crops across the frame, including its far
+    # corner (row and column offsets near 2^31 / 46340), and by the any-size invariants.
+    ny = nx = 46340
+    assert ny * nx < 2 ** 31
+    g = torch.Generator(device="cuda").manual_seed(46340)
+    f = torch.randn((ny, nx), generator=g, device="cuda").mul_(11.0).add_(120.0)
+    idx = torch.randint(0, ny * nx, (ny * nx // 150,), generator=g, device="cuda")
+    f.view(-1).index_add_(0, idx, torch.rand(idx.numel(), generator=g, device="cuda").mul_(3000.0).add_(200.0))
+    frame = f.round_().clamp_(0, 65535).to(torch.int32).to(torch.int16).view(torch.uint16)
+    del f, idx
+    mask = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    clean = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+    p = lacos.make_params(1.0, 1.5, niter=4)
+    with lacos.Context(0, hbm_budget_bytes=8 << 30) as ctx:
+        r = ctx.wait(ctx.submit(frame, p, mask, clean))
+    torch.cuda.synchronize()
+    assert r.status == 0 and r.n_flagged == int(mask.sum(dtype=torch.int64))
+    keep = mask == 0  # (boolean indexing through the int16 view: uint16 has no CUDA index kernel)
+    assert torch.equal(clean[keep], frame.view(torch.int16)[keep].to(torch.int32).bitwise_and_(0xFFFF).to(torch.float32))
+    rng = np.random.default_rng(46340)
+    size, margin = 40, 64
+    boxes = [(0, size, 0, size), (ny - size, ny, nx - size, nx), (ny - size, ny, 0, size)]
+    boxes += [(int(y), int(y) + size, int(x), int(x) + size) for y, x in rng.integers(0, ny - size, (3, 2))]
+    for (y0, y1, x0, x1) in boxes:
+        cy0, cy1, cx0, cx1 = max(0, y0 - margin), min(ny, y1 + margin), max(0, x0 - margin), min(nx, x1 + margin)
+        crop = frame[cy0:cy1, cx0:cx1].cpu().view(torch.int16).numpy().view(np.uint16).copy()
+        m_ref, c_ref, _, _ = oracle.run(crop, 1.0, 1.5, niter=4)
+        sy, sx = slice(y0 - cy0, y1 - cy0), slice(x0 - cx0, x1 - cx0)
+        assert np.array_equal(mask[y0:y1, x0:x1].cpu().numpy(), m_ref[sy, sx]), (y0, x0)
+        assert np.array_equal(clean[y0:y1, x0:x1].cpu().numpy().view(np.uint32), c_ref[sy, sx].view(np.uint32)), (y0, x0)

@@ -185,6 +185,15 @@ def test_argument_errors(ctx):
         with pytest.raises(lacos.LacosError) as e:
             ctx.submit(f, lacos.make_params(**kw), m, c)
         assert e.value.code == lacos.EINVAL
+    # a frame of 2^31 pixels or more is refused by the C ABI before any device access
+    # (the call gets a small real buffer with the oversize dimensions)
+    import ctypes
+    lib = lacos.load_library()
+    t = ctypes.c_ulonglong(0)
+    p0 = lacos.make_params(1.0, 1.5)
+    rc = lib.lacos_submit(ctx.h, ctypes.c_void_p(f.data_ptr()), lacos.LACOS_F32, 46341, 46341, ctypes.byref(p0),
+                          ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(c.data_ptr()), None, ctypes.byref(t))
+    assert rc == lacos.EINVAL
     p = lacos.make_params(1.0, 1.5)
     p.sepmed = 2  # only 0 or 1
     with pytest.raises(lacos.LacosError) as e:
