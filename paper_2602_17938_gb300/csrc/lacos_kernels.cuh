@@ -1,31 +1,34 @@
 // Device code of the L.A.Cosmic detect-and-clean iteration (sm_103a).
 //
 // Iteration k is two kernels:
-//   core_kernel: per TH x TW tile, stages the original frame X0 and the
-//     cumulative mask M_{k-1} with a 6-pixel halo and rebuilds the working
-//     image I_{k-1} = R(X0, M_{k-1}) on the tile + 4 (step 7 of the previous
-//     iteration: unflagged pixels keep X0, flagged ones take the masked
-//     median of unflagged X0, so I depends only on X0 and the mask); then
-//     L+, N and S densely on the tile + 2 and med3(I) on the tile + 3
-//     (register blocks of shared min/max networks), S' = S - med5(S) from a
-//     compacted list of the pixels where S exceeds the lower threshold, and
-//     F with the objlim test from a compacted list of the unsaturated pixels
-//     where S' exceeds sigclip (steps 1-5).  It writes three bit-planes:
-//     S' > sigclip and S' > sigfrac*sigclip (both excluding saturated
-//     pixels) and the candidates;
-//   grow_kernel: step 6 on 32-pixel words, M_k = M_{k-1} | g2 and the count
-//     of newly flagged pixels.
+//   core_kernel (one per frame dtype): per TH x TW tile, stages the original
+//     frame X0 and the cumulative mask M_{k-1} with a 6-pixel halo and
+//     rebuilds the working image I_{k-1} = R(X0, M_{k-1}) on the tile + 4
+//     (step 7 of the previous iteration: unflagged pixels keep X0, flagged
+//     ones take the masked median of unflagged X0, so I depends only on X0
+//     and the mask); then med5(I) on the tile + 2 and med3(I) on the tile + 3
+//     (register blocks of shared min/max networks), L+, N and S per pixel,
+//     and S' = S - med5(S) with F and the objlim test on compacted lists of
+//     the pixels where a test can pass (steps 1-5).  It writes three
+//     bit-planes: S' > sigclip and S' > sigfrac*sigclip (both excluding
+//     saturated pixels) and the candidates.  Levels after the first skip the
+//     tiles whose inputs did not change;
+//   grow_kernel: step 6 on 32-pixel words, M_k = M_{k-1} | g2, whether the
+//     level found new pixels, and the tiles the next level must recompute.
 // For uint16 frames 2N and 1/(2N) are read from a 65536-entry table indexed by
 // med5, built once per request (ntab_kernel), S = L+/(2N) is formed from the
 // reciprocal with two Markstein corrections (div_recip), and the dense
-// networks run on packed pairs.
+// networks run on packed pairs.  With saturated-star protection the grown
+// saturated set is built once per request (satseed_kernel, satgrow_kernel).
 // finalize_kernel writes the cleaned frame R(X0, M) and the uint8 mask.
 //
 // Every stage evaluates its own array at in-frame positions only and reads
 // out-of-frame neighbours at clamped coordinates (clamp-to-edge per stage).
 //
 // Exactness: all float arithmetic uses the explicit round-to-nearest
-// intrinsics in the same operation order as the float32 CPU definition, the
+// intrinsics in the same operation order as the float32 CPU definition (the
+// uint16 path divides through a reciprocal form that rounds like IEEE division:
+// Markstein's theorem, checked exhaustively by lacos_selftest_division), the
 // translation unit is compiled with -fmad=false, and medians are selections
 // (min/max networks), so results are bit-identical to it.
 #pragma once
