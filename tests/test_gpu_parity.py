@@ -194,6 +194,10 @@ def test_argument_errors(ctx):
     rc = lib.lacos_submit(ctx.h, ctypes.c_void_p(f.data_ptr()), lacos.LACOS_F32, 46341, 46341, ctypes.byref(p0),
                           ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(c.data_ptr()), None, ctypes.byref(t))
     assert rc == lacos.EINVAL
+    for ny, nx in ((0, 16), (16, 0), (-1, 16)):  # empty and negative extents
+        rc = lib.lacos_submit(ctx.h, ctypes.c_void_p(f.data_ptr()), lacos.LACOS_F32, ny, nx, ctypes.byref(p0),
+                              ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(c.data_ptr()), None, ctypes.byref(t))
+        assert rc == lacos.EINVAL, (ny, nx)
     p = lacos.make_params(1.0, 1.5)
     p.sepmed = 2  # only 0 or 1
     with pytest.raises(lacos.LacosError) as e:
