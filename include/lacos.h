@@ -123,7 +123,8 @@ int lacos_submit_async(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny
  * the slot's own stream; lacos_poll/lacos_wait report completion once the
  * host outputs are written.  Requests submitted back to back use different
  * slots and streams, so one frame's upload, another's compute and a third's
- * download overlap (separate copy engines).
+ * download overlap (separate copy engines); the kernels of host requests run
+ * in submission order, one request at a time, rather than concurrently.
  *   h_frame : in, ny*nx host pixels (LACOS_F32 float32 or LACOS_U16 uint16)
  *   h_mask  : out, ny*nx uint8 host mask
  *   h_clean : out, ny*nx float32 host cleaned frame

@@ -12,6 +12,12 @@
 // (each core kernel only where the request has frames of its dtype).
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
+// Host-to-host requests run on their slot's own stream with the frame's
+// upload before and the outputs' download after that sequence; their kernel
+// sequences are chained through one context event (each waits for the
+// previous host request's finalize_kernel), so that requests in flight run
+// their kernels one after another while the copies of the requests before
+// and after overlap them, instead of sharing the SMs and finishing together.
 // Iteration control is on the device: an iteration whose predecessor
 // flagged nothing returns at once, so the host never waits mid-request.
 #include <cuda_runtime.h>
@@ -134,6 +140,7 @@ struct lacos_ctx {
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
+  cudaEvent_t host_chain = nullptr;     // end of the last host request's kernels
 };
 
 using CoreFn = void (*)(const FrameDesc*, int, unsigned, unsigned, int, unsigned*);
@@ -197,8 +204,12 @@ static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
   }
 }
 
+// `chain`, when given, is waited on before the first kernel (after the
+// descriptor copy and memsets, which touch only this slot's scratch) and
+// recorded after finalize_kernel (before the state copy, which may queue
+// behind another request's download).
 static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, const Layout& L,
-                   cudaStream_t s, bool prof) {
+                   cudaStream_t s, bool prof, cudaEvent_t chain = nullptr) {
   char* d = (char*)sl.dscratch;
   unsigned* heads = (unsigned*)(d + L.heads);
   FrameDesc* ddesc = (FrameDesc*)(d + L.descs);
@@ -288,6 +299,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
   // [2n+1] after finalize.
   const int nev = 2 * max_niter + 2;
+  if (chain) CK(cudaStreamWaitEvent(s, chain, 0));
   if (prof) {
     while ((int)sl.prof_ev.size() < nev) {
       cudaEvent_t e;
@@ -324,6 +336,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, nf, total, heads + kHeadFinal);
   CK(cudaGetLastError());
   if (int rc = mark(2 * max_niter + 1)) return rc;
+  if (chain) CK(cudaEventRecord(chain, s));
   sl.prof_n = prof ? max_niter : -1;
   FrameState* hstate = (FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * fr.size()));
   CK(cudaMemcpyAsync(hstate, dstate, sizeof(FrameState) * fr.size(), cudaMemcpyDeviceToHost, s));
@@ -399,6 +412,7 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStr
     CK(cudaMallocHost(&sl->hpinned, hneed));
     sl->hcap = hneed;
   }
+  if (hio && !c->host_chain) CK(cudaEventCreateWithFlags(&c->host_chain, cudaEventDisableTiming));
   if (!sl->ev_start) CK(cudaEventCreate(&sl->ev_start));
   if (!sl->ev_done) CK(cudaEventCreate(&sl->ev_done));
   CK(cudaEventRecord(sl->ev_start, s));
@@ -428,7 +442,7 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStr
     if (hio)
       CK(cudaMemcpyAsync((void*)fr[0].frame, hio->frame, npx * (fr[0].dtype == LACOS_U16 ? 2 : 4),
                          cudaMemcpyHostToDevice, s));
-    rc = enqueue(c, *sl, fr, L, s, c->profiling);
+    rc = enqueue(c, *sl, fr, L, s, c->profiling, hio ? c->host_chain : nullptr);
     if (rc != LACOS_OK) return rc;
     if (hio) {
       CK(cudaMemcpyAsync(hio->mask, fr[0].mask, npx, cudaMemcpyDeviceToHost, s));
@@ -693,6 +707,7 @@ int lacos_destroy(lacos_ctx* c) {
     if (sl.cap_stream) cudaStreamDestroy(sl.cap_stream);
     if (sl.own_stream) cudaStreamDestroy(sl.own_stream);
   }
+  if (c->host_chain) cudaEventDestroy(c->host_chain);
   delete c;
   return rc;
 }
