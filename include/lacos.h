@@ -123,8 +123,11 @@ int lacos_submit_async(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny
  * the slot's own stream; lacos_poll/lacos_wait report completion once the
  * host outputs are written.  Requests submitted back to back use different
  * slots and streams, so one frame's upload, another's compute and a third's
- * download overlap (separate copy engines); the kernels of host requests run
- * in submission order, one request at a time, rather than concurrently.
+ * download overlap (separate copy engines).  Frames of at least 8 x the
+ * GPU's resident core CTAs in 32x64 tiles (about 10 Mpx on 152 SMs) run
+ * their kernels in submission order, one such request at a time, so that
+ * the copies overlap compute; smaller frames run concurrently, and several
+ * more in flight raise their throughput.
  *   h_frame : in, ny*nx host pixels (LACOS_F32 float32 or LACOS_U16 uint16)
  *   h_mask  : out, ny*nx uint8 host mask
  *   h_clean : out, ny*nx float32 host cleaned frame

@@ -13,11 +13,14 @@
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
 // Host-to-host requests run on their slot's own stream with the frame's
-// upload before and the outputs' download after that sequence; their kernel
-// sequences are chained through one context event (each waits for the
-// previous host request's finalize_kernel), so that requests in flight run
-// their kernels one after another while the copies of the requests before
-// and after overlap them, instead of sharing the SMs and finishing together.
+// upload before and the outputs' download after that sequence.  The kernel
+// sequences of host requests whose frame fills the GPU kChainWaves times
+// over are chained through one context event (each waits for the previous
+// such request's finalize_kernel), so that requests in flight run their
+// kernels one after another while the copies of the requests before and
+// after overlap them, instead of sharing the SMs, finishing together and
+// then downloading back to back.  Smaller frames cannot fill the GPU alone
+// and keep running concurrently.
 // Iteration control is on the device: an iteration whose predecessor
 // flagged nothing returns at once, so the host never waits mid-request.
 #include <cuda_runtime.h>
@@ -142,6 +145,10 @@ struct lacos_ctx {
   lacos_profile last_prof{};
   cudaEvent_t host_chain = nullptr;     // end of the last host request's kernels
 };
+
+// A host request is chained when its tiles number at least kChainWaves
+// times the resident core CTAs.
+constexpr unsigned kChainWaves = 8;
 
 using CoreFn = void (*)(const FrameDesc*, int, unsigned, unsigned, int, unsigned*);
 // Core-kernel variants by frame dtype (LACOS_F32, LACOS_U16): register
@@ -442,7 +449,13 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStr
     if (hio)
       CK(cudaMemcpyAsync((void*)fr[0].frame, hio->frame, npx * (fr[0].dtype == LACOS_U16 ? 2 : 4),
                          cudaMemcpyHostToDevice, s));
-    rc = enqueue(c, *sl, fr, L, s, c->profiling, hio ? c->host_chain : nullptr);
+    bool chain = false;
+    if (hio) {
+      const unsigned tiles = (unsigned)((fr[0].ny + TH - 1) / TH) * (unsigned)((fr[0].nx + TW - 1) / TW);
+      const unsigned resident = (unsigned)c->num_sms * (unsigned)c->blocks_per_sm_core_v[fr[0].dtype][c->core_variant];
+      chain = tiles >= kChainWaves * resident;
+    }
+    rc = enqueue(c, *sl, fr, L, s, c->profiling, chain ? c->host_chain : nullptr);
     if (rc != LACOS_OK) return rc;
     if (hio) {
       CK(cudaMemcpyAsync(hio->mask, fr[0].mask, npx, cudaMemcpyDeviceToHost, s));
