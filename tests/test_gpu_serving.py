@@ -162,3 +162,31 @@ def test_host_requests_match_device_requests(lib, dtype):
         for i in range(len(frames)):
             assert torch.equal(h_masks[i], ref[i][0])
             assert torch.equal(h_cleans[i].view(torch.int32), ref[i][1].view(torch.int32))
+
+
+def test_chained_and_concurrent_host_requests_match_device_requests(lib):
+    # Host frames of 8 or more GPU waves of 32x64 tiles run their kernels one
+    # request at a time (2688 x 4096 = 5376 tiles; 8 waves of 152 SMs x 4 CTAs
+    # are 4864); the small frame runs concurrently beside them.
+    lacos = lib
+    specs = [(2688, 4096, np.uint16), (300, 410, np.float32), (2688, 4096, np.float32)]
+    frames = [_frame(ny, nx, 90 + i, dt) for i, (ny, nx, dt) in enumerate(specs)]
+    p = lacos.make_params(1.0, 1.5, niter=4)
+    with lacos.Context(0) as ctx:
+        ref = []
+        for f in frames:
+            d = lacos.to_device(f)
+            m = torch.empty(f.shape, dtype=torch.uint8, device="cuda")
+            c = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+            r = ctx.wait(ctx.submit(d, p, m, c))
+            ref.append((m.cpu(), c.cpu(), r))
+        h_frames = [torch.from_numpy(f.view(np.int16)).pin_memory().view(torch.uint16) if f.dtype == np.uint16
+                    else torch.from_numpy(f).pin_memory() for f in frames]
+        order = [0, 1, 2, 0, 2, 1, 0, 2]
+        h_masks = [torch.zeros(frames[j].shape, dtype=torch.uint8).pin_memory() for j in order]
+        h_cleans = [torch.zeros(frames[j].shape, dtype=torch.float32).pin_memory() for j in order]
+        res = lacos.clean_host_stream(ctx, [h_frames[j] for j in order], p, h_masks, h_cleans, depth=3)
+        for k, j in enumerate(order):
+            assert res[k].status == 0 and res[k].n_flagged == ref[j][2].n_flagged, (k, j)
+            assert torch.equal(h_masks[k], ref[j][0]), (k, j)
+            assert torch.equal(h_cleans[k].view(torch.int32), ref[j][1].view(torch.int32)), (k, j)
