@@ -50,7 +50,10 @@ def _load():
             i, f, ll = ctypes.c_int, ctypes.c_float, ctypes.c_longlong
             for suf in ("f32", "f64"):
                 fn = getattr(lib, f"oracle_run_{suf}")
-                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, i, i, P, P, P, P]
+                fn.argtypes = [P, i, i, i, f, f, f, f, f, f, i, i, i, i, P, P, P, P, P, P]
+                fn.restype = i
+                fn = getattr(lib, f"oracle_estimate_gain_{suf}")
+                fn.argtypes = [P, P, P, i, i, f, P, P, P]
                 fn.restype = i
                 fn = getattr(lib, f"oracle_iterate_{suf}")
                 fn.argtypes = [P, P, i, i, f, f, f, f, f, i, P, P] + [P] * 12
@@ -84,8 +87,12 @@ def _dt(precision: str):
 
 def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 65535.0,
         sigclip: float = 4.5, sigfrac: float = 0.3, objlim: float = 5.0, niter: int = 4,
-        fnorm: bool = True, precision: str = "f32", satgrow: int = 0, sepmed: bool = False):
-    """Full detect-and-clean loop.  Returns (mask u8, cleaned, iters_run, n_flagged).
+        fnorm: bool = True, precision: str = "f32", satgrow: int = 0, sepmed: bool = False,
+        return_gain: bool = False):
+    """Full detect-and-clean loop.  Returns (mask u8, cleaned, iters_run, n_flagged),
+    and with return_gain also the gain of the last iteration run and whether every
+    iteration's gain estimate was defined.
+    gain: 0 estimates it at every iteration (reading C15, uint16 frames only).
     satgrow: radius of the protected square around saturated pixels (reading C16).
     sepmed: both 5x5 detection medians taken separably (comparison mode, reading C17)."""
     lib = _load()
@@ -102,13 +109,38 @@ def run(frame: np.ndarray, gain: float, readnoise: float, satlevel: float = 6553
     clean = np.zeros((ny, nx), T)
     it = ctypes.c_int(0)
     nf = ctypes.c_longlong(0)
+    g_last = ctypes.c_double(0.0)
+    g_ok = ctypes.c_int(0)
     rc = getattr(lib, f"oracle_run_{suf}")(
         _ptr(frame), dtype, ny, nx, gain, readnoise, satlevel, sigclip, sigfrac, objlim,
         int(niter), int(bool(fnorm)), int(satgrow), int(bool(sepmed)), _ptr(mask), _ptr(clean), ctypes.byref(it),
-        ctypes.byref(nf))
+        ctypes.byref(nf), ctypes.byref(g_last), ctypes.byref(g_ok))
     if rc != 0:
         raise ValueError(f"oracle_run_{suf} failed with code {rc}")
+    if return_gain:
+        return mask, clean, it.value, nf.value, g_last.value, bool(g_ok.value)
     return mask, clean, it.value, nf.value
+
+
+def estimate_gain(I: np.ndarray, M: np.ndarray, sat: np.ndarray, readnoise: float,
+                  precision: str = "f32"):
+    """Reading C15 on one image: the gain estimated from the adjacent pixel pairs of I
+    that M and sat leave.  Returns (gain or None when undefined, clipping rounds,
+    (n, sum d, sum d^2, sum(a+b)) of the final pair set)."""
+    lib = _load()
+    T, suf = _dt(precision)
+    I = np.ascontiguousarray(I, T)
+    M = np.ascontiguousarray(M, np.uint8)
+    sat = np.ascontiguousarray(sat, np.uint8)
+    ny, nx = I.shape
+    g = ctypes.c_double(0.0)
+    rounds = ctypes.c_int(0)
+    stats = np.zeros(4, np.int64)
+    rc = getattr(lib, f"oracle_estimate_gain_{suf}")(_ptr(I), _ptr(M), _ptr(sat), ny, nx, readnoise,
+                                                      ctypes.byref(g), ctypes.byref(rounds), _ptr(stats))
+    if rc < 0:
+        raise ValueError("gain estimation needs integer pixel values")
+    return (g.value if rc == 1 else None), rounds.value, tuple(int(v) for v in stats)
 
 
 def ingest(frame: np.ndarray, satlevel: float, precision: str = "f32"):

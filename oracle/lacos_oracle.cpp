@@ -20,8 +20,11 @@
 // round-to-nearest.  Step order follows the paper's step list.
 //
 // Parity status: every function is pinned by tests against brute force,
-// closed forms or invariants (see the tests' oracle-pin module).  The only
-// unpinned function is gain estimation (C15), which is not implemented.
+// closed forms, library routines or invariants (see the tests' oracle-pin
+// module).  Gain estimation (C15) follows a reading of this library's own
+// (the paper prints no formula); it is pinned against scipy's sigma clipping,
+// the exact 3-sigma boundary and the gain it recovers from synthetic Poisson
+// frames, not against the paper.
 
 #include <algorithm>
 #include <cmath>
@@ -295,8 +298,87 @@ long long iterate(const T* X0, const uint8_t* sat, int ny, int nx, const Params<
   return fresh;
 }
 
+// Reading C15 (gain estimation; "Main parameters": a gain that is not
+// supplied is estimated at each iteration, with sigma-clipped statistics --
+// the paper names its sigma-clipping helper but prints no formula).  Photon
+// transfer on adjacent pixel pairs of the iteration's image I:
+//  - pairs: columns (2m, 2m+1) of every row, both pixels unflagged in M and
+//    not saturated, so both hold input values; d = a - b;
+//  - clipping: the pair set K_0 holds every such pair; K_(r+1) keeps the pairs
+//    of K_r whose d lies within 3 population standard deviations of K_r's
+//    mean, (n d - S1)^2 <= 9 (n S2 - S1^2) with n = |K_r|, S1 = sum d,
+//    S2 = sum d^2, evaluated exactly in integers; at most 5 such rounds,
+//    stopping once a round keeps every pair (astropy's sigma_clip defaults,
+//    with the mean as centre);
+//  - gain: for a pair of means mu_a, mu_b (ADU), var(d) = (mu_a + mu_b)/g +
+//    2 rn^2/g^2 (Poisson electrons plus read noise, in ADU), so over the
+//    final set V g^2 - A g - 2 n rn^2 = 0 with V = sum (d - mean d)^2 =
+//    (n S2 - S1^2)/n and A = sum (a + b); g is the positive root
+//    (A + sqrt(A^2 + 8 n rn^2 V)) / (2 V), in double in exactly this order.
+// The sums are exact only for integer values, so the estimate is defined
+// for uint16 frames (whose image stays integer: replacements copy input
+// values).  With no pair, or V = 0, the estimate is undefined; the
+// iteration then uses g = 1 and the run reports it.
+struct GainStats {
+  long long n = 0, s1 = 0;
+  unsigned long long s2 = 0, a = 0;
+};
+
+template <class T>
+int estimate_gain(const T* I, const uint8_t* M, const uint8_t* sat, int ny, int nx, double rn,
+                  double* g_out, int* rounds_out, GainStats* final_out) {
+  struct Pair { long long a, b; };
+  std::vector<Pair> pairs;
+  for (int i = 0; i < ny; ++i)
+    for (int j = 0; j + 1 < nx; j += 2) {
+      const size_t q = (size_t)i * nx + j;
+      if (M[q] || M[q + 1] || sat[q] || sat[q + 1]) continue;
+      const T va = I[q], vb = I[q + 1];
+      if (!(va >= T(0) && va <= T(65535) && va == std::floor(va))) return -1;
+      if (!(vb >= T(0) && vb <= T(65535) && vb == std::floor(vb))) return -1;
+      pairs.push_back({(long long)va, (long long)vb});
+    }
+  std::vector<uint8_t> kept(pairs.size(), 1);
+  GainStats st, prev;
+  int r = 0;
+  for (r = 0;; ++r) {
+    st = GainStats{};
+    for (size_t t = 0; t < pairs.size(); ++t) {
+      if (!kept[t]) continue;
+      const long long d = pairs[t].a - pairs[t].b;
+      st.n += 1;
+      st.s1 += d;
+      st.s2 += (unsigned long long)(d * d);
+      st.a += (unsigned long long)(pairs[t].a + pairs[t].b);
+    }
+    if (st.n == 0 || r == 5 || (r > 0 && st.n == prev.n)) break;
+    const __int128 n = st.n, s1 = st.s1, s2 = (__int128)st.s2;
+    const __int128 bound = 9 * (n * s2 - s1 * s1);
+    for (size_t t = 0; t < pairs.size(); ++t) {
+      if (!kept[t]) continue;
+      const __int128 e = n * (__int128)(pairs[t].a - pairs[t].b) - s1;
+      if (e * e > bound) kept[t] = 0;
+    }
+    prev = st;
+  }
+  if (rounds_out) *rounds_out = r;
+  if (final_out) *final_out = st;
+  if (st.n < 2) return 0;
+  const __int128 vnum = (__int128)st.n * (__int128)st.s2 - (__int128)st.s1 * (__int128)st.s1;
+  if (vnum <= 0) return 0;
+  const double nd = (double)st.n;
+  const double V = (double)vnum / nd;
+  const double A = (double)st.a;
+  const double rn2 = rn * rn;
+  const double disc = A * A + 8.0 * nd * rn2 * V;
+  const double g = (A + std::sqrt(disc)) / (2.0 * V);
+  if (!(g > 0) || !std::isfinite(g)) return 0;
+  *g_out = g;
+  return 1;
+}
+
 bool params_ok(double gain, double rn, double sigclip, double sigfrac, double objlim, int niter) {
-  if (!(gain > 0) || !(rn >= 0) || !(sigclip > 0) || !(sigfrac > 0) || !(objlim > 0)) return false;
+  if (!(gain >= 0) || !(rn >= 0) || !(sigclip > 0) || !(sigfrac > 0) || !(objlim > 0)) return false;
   if (niter < 0) return false;
   return std::isfinite(gain) && std::isfinite(rn) && std::isfinite(sigclip) &&
          std::isfinite(sigfrac) && std::isfinite(objlim);
@@ -304,11 +386,16 @@ bool params_ok(double gain, double rn, double sigclip, double sigfrac, double ob
 
 // The whole detect-and-clean loop (step a9): repeat until niter iterations
 // or no new pixel (C13).  Output mask is cumulative; cleaned = I.
+// gain = 0 estimates the gain at every iteration (C15, uint16 frames only);
+// *gain_last receives the gain of the last iteration run (the supplied one
+// when gain > 0) and *gain_ok 0 when some iteration's estimate was undefined.
 template <class T>
 int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_t* mask_out,
-        T* clean_out, int* iters_run, long long* n_flagged) {
+        T* clean_out, int* iters_run, long long* n_flagged, double* gain_last, int* gain_ok) {
   if (!frame || ny < 1 || nx < 1 || (dtype != 0 && dtype != 1)) return -1;
   if (!params_ok(p.gain, p.readnoise, p.sigclip, p.sigfrac, p.objlim, p.niter)) return -1;
+  const bool estimate = p.gain == T(0);
+  if (estimate && dtype != 1) return -1;
   if (p.satgrow < 0 || p.satgrow > 4 || (p.sepmed != 0 && p.sepmed != 1)) return -1;
   const size_t n = (size_t)ny * nx;
   std::vector<T> X0;
@@ -322,12 +409,24 @@ int run(const void* frame, int dtype, int ny, int nx, const Params<T>& p, uint8_
   }
   std::vector<T> I(X0);
   std::vector<uint8_t> M(n, 0);
+  Params<T> pk = p;
+  int ok = 1;
   int k = 0;
   for (k = 1; k <= p.niter; ++k) {
-    const long long fresh = iterate(X0.data(), sat.data(), ny, nx, p, I.data(), M.data(),
+    if (estimate) {  // C15: the gain of iteration k from I_k and M_(k-1)
+      double g = 0.0;
+      const int e = estimate_gain(I.data(), M.data(), sat.data(), ny, nx, (double)p.readnoise, &g,
+                                  nullptr, nullptr);
+      if (e < 0) return -1;
+      if (e == 0) ok = 0;
+      pk.gain = e == 1 ? (T)g : T(1);
+    }
+    const long long fresh = iterate(X0.data(), sat.data(), ny, nx, pk, I.data(), M.data(),
                                     (const Dumps<T>*)nullptr);
     if (fresh == 0) break;
   }
+  if (gain_last) *gain_last = (double)pk.gain;
+  if (gain_ok) *gain_ok = ok;
   if (k > p.niter) k = p.niter;
   long long cnt = 0;
   for (size_t q = 0; q < n; ++q) {
@@ -362,22 +461,41 @@ extern "C" {
 int oracle_run_f32(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
                    int fnorm, int satgrow, int sepmed, uint8_t* mask, float* clean, int* iters_run,
-                   long long* n_flagged) {
+                   long long* n_flagged, double* gain_last, int* gain_ok) {
   return run<float>(frame, dtype, ny, nx,
                     make_params<float>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow,
                                        sepmed),
-                    mask, clean, iters_run, n_flagged);
+                    mask, clean, iters_run, n_flagged, gain_last, gain_ok);
 }
 
 int oracle_run_f64(const void* frame, int dtype, int ny, int nx, float gain, float rn,
                    float satlevel, float sigclip, float sigfrac, float objlim, int niter,
                    int fnorm, int satgrow, int sepmed, uint8_t* mask, double* clean, int* iters_run,
-                   long long* n_flagged) {
+                   long long* n_flagged, double* gain_last, int* gain_ok) {
   return run<double>(frame, dtype, ny, nx,
                      make_params<double>(gain, rn, satlevel, sigclip, sigfrac, objlim, niter, fnorm, satgrow,
                                          sepmed),
-                     mask, clean, iters_run, n_flagged);
+                     mask, clean, iters_run, n_flagged, gain_last, gain_ok);
 }
+
+// C15 on one image: I (float or double values), M and sat 0/1 per pixel.
+// Returns 1 with *g set, 0 when undefined, -1 for a non-integer value in a
+// pair.  stats receives n, sum d, sum d^2 and sum (a + b) of the final set.
+#define ORACLE_GAIN(SUF, T)                                                                    \
+  int oracle_estimate_gain_##SUF(const T* I, const uint8_t* M, const uint8_t* sat, int ny,     \
+                                 int nx, float rn, double* g, int* rounds, long long* stats) { \
+    GainStats st;                                                                             \
+    const int e = estimate_gain<T>(I, M, sat, ny, nx, (double)rn, g, rounds, &st);             \
+    if (stats) {                                                                              \
+      stats[0] = st.n;                                                                        \
+      stats[1] = st.s1;                                                                       \
+      stats[2] = (long long)st.s2;                                                            \
+      stats[3] = (long long)st.a;                                                             \
+    }                                                                                         \
+    return e;                                                                                 \
+  }
+ORACLE_GAIN(f32, float)
+ORACLE_GAIN(f64, double)
 
 // One iteration with every intermediate exposed.  X0 and I are in T; sat is
 // 0/1 per pixel.  I and M are updated in place.  Returns the new-pixel count.
