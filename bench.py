@@ -42,7 +42,7 @@ def kernel_source_sha() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("lacos_kernels.cuh", "networks.cuh", "lacos.cu"):
+    for name in ("lacos_kernels.cuh", "networks.cuh", "gain_math.cuh", "lacos.cu"):
         with open(os.path.join(ROOT, "paper_2602_17938_gb300", "csrc", name)) as f:
             for line in f:
                 code = re.sub(r"//.*", "", line).rstrip()

@@ -57,13 +57,26 @@ enum {
   LACOS_ECUDA = -4,           /* a CUDA call failed; see lacos_last_cuda_error */
   LACOS_ENONFINITE = -5,      /* the input held NaN or Inf: outputs undefined */
   LACOS_ETIMEOUT = -6,        /* a bounded device wait gave up */
-  LACOS_EUNKNOWN_TICKET = -7  /* poll on a ticket that is not in flight */
+  LACOS_EUNKNOWN_TICKET = -7, /* poll on a ticket that is not in flight */
+  LACOS_ENOGAIN = -8          /* an estimated gain was undefined at some iteration (no pixel
+                                 pair left, or all their differences equal); that iteration
+                                 used gain 1 */
 };
 
 #define LACOS_MAX_NITER 256
 
 /* Parameters of one frame (dfcosmic "Main parameters" plus gain, readnoise).
- * gain > 0 [e-/ADU]; readnoise >= 0 [e-]; satlevel [ADU], <= 0 disables the
+ * gain > 0 [e-/ADU], or 0 to estimate it at every iteration ("Main
+ * parameters": a gain that is not supplied is estimated per iteration; the
+ * paper gives no formula, so this library's reading is photon transfer on
+ * adjacent pixel pairs).  At iteration k the pairs (columns 2m, 2m+1) whose
+ * pixels are both unflagged so far and unsaturated give d = a - b; d is
+ * clipped at 3 population standard deviations from its mean (exactly, in
+ * integers; at most 5 rounds, stopping when a round keeps every pair), and g
+ * solves V g^2 - A g - 2 n rn^2 = 0 for the n remaining pairs, V the sum of
+ * squared deviations of d and A the sum of a + b, evaluated in double and
+ * rounded to float.  Only uint16 frames (float32 frames with gain 0 are
+ * LACOS_EINVAL).  readnoise >= 0 [e-]; satlevel [ADU], <= 0 disables the
  * saturation guard; sigclip, sigfrac, objlim > 0; 0 <= niter <= 256.
  * fine_norm: 1 divides the fine-structure image by N (default reading),
  * 0 uses max(med3 - med7, 0.01) unnormalised.
@@ -83,10 +96,13 @@ typedef struct {
 } lacos_params;
 
 typedef struct {
-  int status;            /* LACOS_OK or LACOS_ENONFINITE / LACOS_ETIMEOUT */
+  int status;            /* LACOS_OK or LACOS_ENONFINITE / LACOS_ETIMEOUT / LACOS_ENOGAIN */
   int iters_run;         /* iterations executed (early stop included) */
   long long n_flagged;   /* pixels in the final cosmic-ray mask */
   double latency_ms;     /* submit-to-completion on the device (event time) */
+  float gain;            /* the gain of the last iteration run: the supplied one, or the
+                            estimate when gain = 0 (0 if no iteration ran); 0 for the
+                            aggregate of a batch of several frames */
 } lacos_result;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the

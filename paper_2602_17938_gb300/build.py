@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblacos.so")
 PEAK_LIB = os.path.join(OUT_DIR, "libalupeak.so")
 SOURCES = ["lacos.cu"]
-DEPS = ["lacos_kernels.cuh", "networks.cuh", os.path.join("..", "..", "include", "lacos.h")]
+DEPS = ["lacos_kernels.cuh", "networks.cuh", "gain_math.cuh", os.path.join("..", "..", "include", "lacos.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

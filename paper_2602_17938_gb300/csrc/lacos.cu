@@ -84,6 +84,7 @@ struct Slot {
   std::vector<cudaEvent_t> prof_ev;
   int prof_n = -1;  // levels recorded for the request in flight (-1: none)
   std::vector<long long> npix;
+  std::vector<float> gain_in;  // per frame: the supplied gain (0: estimated)
 };
 
 bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) {
@@ -173,7 +174,7 @@ static bool params_valid(const lacos_params* p) {
   const float v[6] = {p->gain, p->readnoise, p->satlevel, p->sigclip, p->sigfrac, p->objlim};
   for (float x : v)
     if (!std::isfinite(x)) return false;
-  if (!(p->gain > 0.0f) || !(p->readnoise >= 0.0f) || !(p->sigclip > 0.0f) ||
+  if (!(p->gain >= 0.0f) || !(p->readnoise >= 0.0f) || !(p->sigclip > 0.0f) ||
       !(p->sigfrac > 0.0f) || !(p->objlim > 0.0f))
     return false;
   if (p->niter < 0 || p->niter > LACOS_MAX_NITER) return false;
@@ -188,6 +189,7 @@ static bool frame_valid(const FrameReq& f) {
   if (f.dtype != LACOS_F32 && f.dtype != LACOS_U16) return false;
   if (f.ny < 1 || f.nx < 1) return false;
   if ((long long)f.ny * (long long)f.nx >= (1LL << 31)) return false;
+  if (f.p.gain == 0.0f && f.dtype != LACOS_U16) return false;  // estimated gain: integer frames only
   return params_valid(&f.p);
 }
 
@@ -209,6 +211,14 @@ static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
       sl.iocap = 0;
     }
   }
+}
+
+// Gain estimation (frames with gain 0) at level k: the pair-sum passes, then
+// the N table where the gain changed.  Two CTAs per SM per frame.
+static void launch_gain_level(const FrameDesc* ddesc, int nf, int k, int num_sms, cudaStream_t s) {
+  const dim3 grid((unsigned)(2 * num_sms), (unsigned)nf);
+  for (int r = 0; r < kGainPasses; ++r) gain_pass_kernel<<<grid, NT, 0, s>>>(ddesc, nf, k, r);
+  ntab_level_kernel<<<dim3(256, (unsigned)nf), 256, 0, s>>>(ddesc, nf, k);
 }
 
 // `chain`, when given, is waited on before the first kernel (after the
@@ -236,6 +246,7 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     for (size_t i = 0; i < fr.size(); ++i)
       if (fr[i].dtype == dt) order.push_back(i);
   unsigned tiles_u16 = 0;
+  bool any_est = false;
   for (size_t j = 0; j < fr.size(); ++j) {
     const size_t i = order[j];
     const FrameReq& f = fr[i];
@@ -260,6 +271,9 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.clean_out = f.clean;
     h.st = dstate + i;
     h.gain = f.p.gain;
+    h.gain_est = f.p.gain == 0.0f;
+    any_est = any_est || h.gain_est;
+    h.rn = f.p.readnoise;
     volatile float rn = f.p.readnoise;
     volatile float rn2 = rn * rn;  // float product, as the float32 definition
     h.rn2 = rn2;
@@ -329,6 +343,10 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   }
   CK(cudaGetLastError());
   for (int k = 1; k <= max_niter; ++k) {
+    if (any_est) {
+      launch_gain_level(ddesc, nf, k, c->num_sms, s);
+      CK(cudaGetLastError());
+    }
     for (int dt : {1, 0}) {
       if (!gdt[dt]) continue;
       kCoreVariants[dt][cv]<<<gdt[dt], NT, kCoreSmem[dt], s>>>(ddesc, nf, rng[dt][0], rng[dt][1], k,
@@ -466,7 +484,11 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStr
   sl->busy = true;
   sl->nframes = (int)fr.size();
   sl->npix.resize(fr.size());
-  for (size_t i = 0; i < fr.size(); ++i) sl->npix[i] = (long long)fr[i].ny * fr[i].nx;
+  sl->gain_in.resize(fr.size());
+  for (size_t i = 0; i < fr.size(); ++i) {
+    sl->npix[i] = (long long)fr[i].ny * fr[i].nx;
+    sl->gain_in[i] = fr[i].p.gain;
+  }
   sl->per_frame = per_frame;
   sl->ticket = c->next_ticket++;
   *ticket = sl->ticket;
@@ -477,7 +499,7 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, sl.ev_start, sl.ev_done);
   const FrameState* hs = (const FrameState*)((char*)sl.hpinned + align_up(sizeof(FrameDesc) * sl.nframes));
-  lacos_result agg{LACOS_OK, 0, 0, (double)ms};
+  lacos_result agg{LACOS_OK, 0, 0, (double)ms, 0.0f};
   if (sl.prof_n >= 0) {
     lacos_profile& P = c->last_prof;
     std::memset(&P, 0, sizeof(P));
@@ -498,13 +520,16 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
     }
   }
   for (int i = 0; i < sl.nframes; ++i) {
-    lacos_result r{LACOS_OK, hs[i].iters_run, (long long)hs[i].flagged, (double)ms};
+    lacos_result r{LACOS_OK, hs[i].iters_run, (long long)hs[i].flagged, (double)ms, 0.0f};
+    r.gain = sl.gain_in[i] > 0.0f ? sl.gain_in[i] : hs[i].gain;
     if (hs[i].err & ERR_NONFINITE) r.status = LACOS_ENONFINITE;
     else if (hs[i].err & ERR_TIMEOUT) r.status = LACOS_ETIMEOUT;
+    else if (hs[i].err & ERR_NOGAIN) r.status = LACOS_ENOGAIN;
     if (sl.per_frame) sl.per_frame[i] = r;
     if (agg.status == LACOS_OK) agg.status = r.status;
     agg.iters_run = std::max(agg.iters_run, r.iters_run);
     agg.n_flagged += r.n_flagged;
+    agg.gain = sl.nframes == 1 ? r.gain : 0.0f;
   }
   if (res) *res = agg;
   sl.busy = false;
@@ -832,6 +857,8 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.clean_out = d_clean;
   h.st = dstate;
   h.gain = p->gain;
+  h.gain_est = p->gain == 0.0f;
+  h.rn = p->readnoise;
   volatile float rn = p->readnoise;
   volatile float rn2 = rn * rn;
   h.rn2 = rn2;
@@ -873,6 +900,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
     satgrow_kernel<<<(nw + 255) / 256, 256, 0, s>>>(ddesc, 0, nw);
   }
   for (int k = 1; k <= p->niter; ++k) {
+    if (h.gain_est) launch_gain_level(ddesc, 1, k, sd->num_sms, s);
     kCoreVariants[di][sd->core_variant]<<<gd, NT, kCoreSmem[di], s>>>(ddesc, 1, 0, total, k,
                                                                       heads + kHeadCore + di * kHeadLevels + k);
     grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, 1, total_gblk, k);
@@ -884,8 +912,11 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
       cudaStreamSynchronize(s) != cudaSuccess)
     return LACOS_ECUDA;
   if (res) {
-    res->status = (hs.err & ERR_NONFINITE) ? LACOS_ENONFINITE
-                                           : ((hs.err & ERR_TIMEOUT) ? LACOS_ETIMEOUT : LACOS_OK);
+    res->status = (hs.err & ERR_NONFINITE)  ? LACOS_ENONFINITE
+                  : (hs.err & ERR_TIMEOUT) ? LACOS_ETIMEOUT
+                  : (hs.err & ERR_NOGAIN)  ? LACOS_ENOGAIN
+                                           : LACOS_OK;
+    res->gain = h.gain_est ? hs.gain : p->gain;
     res->iters_run = hs.iters_run;
     res->n_flagged = (long long)hs.flagged;
     res->latency_ms = 0.0;

@@ -69,6 +69,7 @@ __device__ __forceinline__ U16x2 MX(U16x2 a, U16x2 b) {
 }
 
 #include "networks.cuh"
+#include "gain_math.cuh"
 
 namespace lacos {
 
@@ -79,6 +80,11 @@ constexpr int NT = 256;  // threads per CTA
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
+constexpr unsigned ERR_NOGAIN = 4u;  // a level's gain estimate was undefined (it used gain 1)
+
+// Gain estimation (C15): passes over the pair set per level -- the full set
+// and up to five clipping rounds.
+constexpr int kGainPasses = 6;
 
 struct FrameState {
   unsigned long long fresh[LACOS_MAX_NITER + 1];  // nonzero when iteration k flagged new pixels
@@ -88,6 +94,16 @@ struct FrameState {
   unsigned long long px_core;                      // tile pixels the core kernel computed (all levels)
   unsigned int err;
   int iters_run;
+  // Gain estimation (frames with gain 0), per level: the pair sums of each
+  // pass (n, sum d as two's complement, sum d^2, sum (a + b)), the blocks of
+  // each pass that have added theirs, the clip interval of d for the next
+  // pass, the level whose estimate is final, the level whose core launch
+  // recomputes every tile (the gain changed), and the latest level's gain.
+  unsigned long long gsum[kGainPasses][4];
+  unsigned int gblocks[kGainPasses];
+  long long g_lo, g_hi;
+  int g_level_done, g_all_level;
+  float gain;
 };
 
 struct FrameDesc {
@@ -106,6 +122,8 @@ struct FrameDesc {
   float* clean_out;  // the working image I, and the cleaned output
   FrameState* st;
   float gain, rn2, satlevel, sigclip, lo, thr_min, objlim;
+  float rn;          // read noise (the gain estimate squares it in double)
+  int gain_est;      // 1: gain estimated at every level (C15, uint16 frames)
   int niter, fnorm;
   int satgrow;       // radius of the protected region around saturated pixels (0..4)
   int sepmed;        // 1: both 5x5 detection medians taken separably (comparison mode)
@@ -373,27 +391,177 @@ __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t
   }
 }
 
-__device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) {
-  const float gm = __fmul_rn(f.gain, m5);
+__device__ __forceinline__ float noise_of_g(float gain, float rn2, float m5) {
+  const float gm = __fmul_rn(gain, m5);
   const float e = gm < 1e-4f ? 1e-4f : gm;
-  return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, f.rn2)), f.gain);
+  return __fdiv_rn(__fsqrt_rn(__fadd_rn(e, rn2)), gain);
 }
+
+__device__ __forceinline__ float noise_of(const FrameDesc& f, float m5) { return noise_of_g(f.gain, f.rn2, m5); }
 
 // {D, y} = {2N, RN(1/D)} for an integer med5 value m (N with the same
 // arithmetic as noise_of; doubling is exact).
-__device__ __forceinline__ float2 ntab_entry(const FrameDesc& f, int m) {
-  const float N = noise_of(f, (float)m);
+__device__ __forceinline__ float2 ntab_entry_g(float gain, float rn2, int m) {
+  const float N = noise_of_g(gain, rn2, (float)m);
   const float D = __fadd_rn(N, N);
   return make_float2(D, __fdiv_rn(1.0f, D));
 }
 
-// The table of a uint16 frame, once per request instead of once per pixel.
+__device__ __forceinline__ float2 ntab_entry(const FrameDesc& f, int m) { return ntab_entry_g(f.gain, f.rn2, m); }
+
+// The table of a uint16 frame, once per request instead of once per pixel
+// (per level, by ntab_level_kernel, when the gain is estimated).
 __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
   const int fi = blockIdx.y;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= nframes || m > 65535) return;
   const FrameDesc& f = fr[fi];
-  if (f.dtype == 1) f.ntab[m] = ntab_entry(f, m);
+  if (f.dtype == 1 && !f.gain_est) f.ntab[m] = ntab_entry(f, m);
+}
+
+// ---- gain estimation (C15), per level, for frames with gain 0 --------------
+//
+// Pass r (0..kGainPasses-1) of level k sums the pairs (columns 2m, 2m+1) of
+// the level's image whose pixels are both unflagged in M_(k-1) and
+// unsaturated -- so both hold input values -- and whose difference d = a - b
+// lies in the clip interval (every d at r = 0): n, sum d, sum d^2, sum (a+b).
+// The last block of a frame to add its sums folds them: when the clipping
+// has converged (the pass kept as many pairs as the one before, or this is
+// the fifth clipping round) it sets the level's gain; otherwise it stores
+// the next interval, the current one intersected with 3 population
+// standard deviations of this pass's set.  No block waits for another: the
+// last block is the one whose arrival completes the count.  Every block of
+// a frame takes the same early exit, since it reads only what earlier
+// launches wrote.
+__global__ void __launch_bounds__(NT) gain_pass_kernel(const FrameDesc* __restrict__ fr, int nframes, int k,
+                                                       int r) {
+  const int fi = blockIdx.y;
+  if (fi >= nframes) return;
+  const FrameDesc& f = fr[fi];
+  FrameState* st = f.st;
+  if (!f.gain_est || !iteration_runs(f, k) || __ldcg(&st->g_level_done) == k) return;
+  long long lo = -65536, hi = 65536;
+  if (r > 0) {
+    lo = __ldcg(&st->g_lo);
+    hi = __ldcg(&st->g_hi);
+  }
+  const uint32_t* Mprev = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;  // M_(k-1)
+  const bool satchk = f.p_sat == nullptr && f.satlevel > 0.0f;
+  // Rows start on 16-byte boundaries and hold whole 8-pixel chunks: each
+  // word's 32 pixels are four 16-byte loads.
+  const bool vec = (reinterpret_cast<uintptr_t>(f.x0) & 15u) == 0 && f.nx % 8 == 0;
+  const unsigned nwords = (unsigned)f.ny * (unsigned)f.wpr;
+  const uint16_t* x0 = static_cast<const uint16_t*>(f.x0);
+  unsigned long long n = 0, s2 = 0, a = 0;
+  long long s1 = 0;
+  for (unsigned w = blockIdx.x * NT + threadIdx.x; w < nwords; w += gridDim.x * NT) {
+    const int y = (int)(w / (unsigned)f.wpr), xw = (int)(w % (unsigned)f.wpr) * 32;
+    const int cnt = min(32, f.nx - xw);  // pixels of this word
+    uint32_t bad = __ldg(Mprev + w);
+    if (f.p_sat) bad |= __ldg(f.p_sat + w);
+    const uint16_t* row = x0 + (size_t)y * f.nx + xw;
+    uint32_t v[16];  // pair m: column xw+2m in the low half, xw+2m+1 in the high half
+    if (vec) {
+      const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < cnt / 8) {
+          const uint4 u = __ldg(src + c);
+          v[4 * c] = u.x;
+          v[4 * c + 1] = u.y;
+          v[4 * c + 2] = u.z;
+          v[4 * c + 3] = u.w;
+        } else {
+          v[4 * c] = v[4 * c + 1] = v[4 * c + 2] = v[4 * c + 3] = 0u;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m)
+        v[m] = 2 * m + 1 < cnt ? (uint32_t)__ldg(row + 2 * m) | ((uint32_t)__ldg(row + 2 * m + 1) << 16) : 0u;
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (2 * m + 1 >= cnt || ((bad >> (2 * m)) & 3u)) continue;
+      const int va = (int)(v[m] & 0xffffu), vb = (int)(v[m] >> 16);
+      if (satchk && ((float)va >= f.satlevel || (float)vb >= f.satlevel)) continue;
+      const int d = va - vb;
+      if (d < lo || d > hi) continue;
+      n += 1;
+      s1 += d;
+      s2 += (unsigned long long)((long long)d * d);
+      a += (unsigned long long)(va + vb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_down_sync(0xffffffffu, n, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    a += __shfl_down_sync(0xffffffffu, a, o);
+  }
+  __shared__ unsigned long long red[NT / 32][4];
+  __shared__ int s_last;
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = n;
+    red[threadIdx.x >> 5][1] = (unsigned long long)s1;
+    red[threadIdx.x >> 5][2] = s2;
+    red[threadIdx.x >> 5][3] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int q = 0; q < NT / 32; ++q)
+      for (int i = 0; i < 4; ++i) t[i] += red[q][i];
+    if (t[0])
+      for (int i = 0; i < 4; ++i) atomicAdd(&st->gsum[r][i], t[i]);
+    __threadfence();
+    s_last = atomicAdd(&st->gblocks[r], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  const unsigned long long n_r = __ldcg(&st->gsum[r][0]);
+  const long long s1_r = (long long)__ldcg(&st->gsum[r][1]);
+  const unsigned long long s2_r = __ldcg(&st->gsum[r][2]), a_r = __ldcg(&st->gsum[r][3]);
+  const bool done = n_r == 0 || r == kGainPasses - 1 || (r > 0 && n_r == __ldcg(&st->gsum[r - 1][0]));
+  if (!done) {
+    long long l, h;
+    lacos_gain::gm_clip_interval(n_r, s1_r, s2_r, &l, &h);
+    st->g_lo = l > lo ? l : lo;
+    st->g_hi = h < hi ? h : hi;
+    return;
+  }
+  double g = 0.0;
+  float gf = 1.0f;
+  if (lacos_gain::gm_gain(n_r, s1_r, s2_r, a_r, f.rn, &g))
+    gf = __double2float_rn(g);
+  else
+    atomicOr(&st->err, ERR_NOGAIN);
+  if (k == 1 || __float_as_uint(gf) != __float_as_uint(__ldcg(&st->gain))) st->g_all_level = k;
+  st->gain = gf;
+  st->g_level_done = k;
+  for (int q = 0; q < kGainPasses; ++q) {  // the next level starts from zero
+    for (int i = 0; i < 4; ++i) st->gsum[q][i] = 0ull;
+    st->gblocks[q] = 0u;
+  }
+}
+
+// At each level where a frame's estimated gain differs from the previous
+// level's (and at the first): its N table for the new gain, and every core
+// tile marked for recomputation at this level (N changes everywhere).
+// Grid: 256 x frames blocks of 256 threads, one table entry per thread,
+// tiles in a grid-stride loop.
+__global__ void ntab_level_kernel(const FrameDesc* __restrict__ fr, int nframes, int k) {
+  const int fi = blockIdx.y;
+  if (fi >= nframes) return;
+  const FrameDesc& f = fr[fi];
+  if (!f.gain_est || !iteration_runs(f, k) || __ldcg(&f.st->g_all_level) != k) return;
+  const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m <= 65535u) f.ntab[m] = ntab_entry_g(__ldcg(&f.st->gain), f.rn2, (int)m);
+  if (k == 1) return;  // level 1 computes every tile anyway
+  uint8_t* marks = f.tflags + (size_t)(k & 1) * tiles_of(f);
+  for (unsigned t = m; t < tiles_of(f); t += gridDim.x * blockDim.x) marks[t] = 1;
 }
 
 // Saturated-star protection (C16), once per request: the seeds (input >=

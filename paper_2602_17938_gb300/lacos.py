@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblacos.so")
 
 LACOS_F32, LACOS_U16 = 0, 1
 OK, PENDING = 0, 1
-EINVAL, EAGAIN, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNKNOWN_TICKET = -1, -2, -3, -4, -5, -6, -7
+EINVAL, EAGAIN, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNKNOWN_TICKET, ENOGAIN = -1, -2, -3, -4, -5, -6, -7, -8
 MAX_NITER = 256
 _ERRNAMES = {EINVAL: "EINVAL", EAGAIN: "EAGAIN", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
-             ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT", EUNKNOWN_TICKET: "EUNKNOWN_TICKET"}
+             ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT", EUNKNOWN_TICKET: "EUNKNOWN_TICKET",
+             ENOGAIN: "ENOGAIN"}
 
 
 class LacosError(RuntimeError):
@@ -50,11 +51,13 @@ class Profile(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters_run", ctypes.c_int),
-                ("n_flagged", ctypes.c_longlong), ("latency_ms", ctypes.c_double)]
+                ("n_flagged", ctypes.c_longlong), ("latency_ms", ctypes.c_double),
+                ("gain", ctypes.c_float)]
 
 
 def make_params(gain, readnoise, satlevel=65535.0, sigclip=4.5, sigfrac=0.3, objlim=5.0,
                 niter=4, fine_norm=True, satgrow=0, sepmed=False) -> Params:
+    """Frame parameters; gain 0 estimates the gain at every iteration (uint16 frames)."""
     return Params(gain, readnoise, satlevel, sigclip, sigfrac, objlim, int(niter), int(bool(fine_norm)),
                   int(satgrow), int(bool(sepmed)))
 
@@ -125,6 +128,7 @@ class FrameResult:
     iters_run: int
     n_flagged: int
     latency_ms: float
+    gain: float = 0.0  # the last iteration's gain (the estimate when the gain was 0)
 
 
 class Context:
@@ -232,14 +236,14 @@ class Context:
             return None
         if rc != OK:
             raise LacosError(rc, "lacos_poll")
-        return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms)
+        return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms, r.gain)
 
     def wait(self, ticket: int) -> FrameResult:
         r = Result()
         rc = self.lib.lacos_wait(self.h, ticket, ctypes.byref(r))
         if rc != OK:
             raise LacosError(rc, "lacos_wait")
-        return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms)
+        return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms, r.gain)
 
     def set_profiling(self, on: bool):
         rc = self.lib.lacos_set_profiling(self.h, int(bool(on)))
@@ -326,7 +330,7 @@ def run_static(frame, params: Params, mask, clean, stream=None) -> FrameResult:
                                          ctypes.byref(r))
     if rc != OK:
         raise LacosError(rc, "lacos_run_static")
-    return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms)
+    return FrameResult(r.status, r.iters_run, r.n_flagged, r.latency_ms, r.gain)
 
 
 def clean_host(h_frame, params: Params, h_mask, h_clean, ctx: Context):
