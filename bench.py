@@ -348,9 +348,12 @@ def run_ours(args):
 
     # Optional modes on the same frame, timed the same way (device, L2 flushed).
     modes = {}
-    for name, extra in (("default", dict()), ("satgrow2", dict(satgrow=2)), ("sepmed", dict(sepmed=True))):
-        mp = lacos.make_params(spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac,
-                               spec.objlim, spec.niter, True, **extra)
+    for name, extra in (("default", dict()), ("satgrow2", dict(satgrow=2)), ("sepmed", dict(sepmed=True)),
+                        ("gain_estimated", dict(gain=0.0))):
+        kw = dict(gain=spec.gain, readnoise=spec.readnoise, satlevel=spec.satlevel, sigclip=spec.sigclip,
+                  sigfrac=spec.sigfrac, objlim=spec.objlim, niter=spec.niter, fine_norm=True)
+        kw.update(extra)
+        mp = lacos.make_params(**kw)
         for _ in range(2):
             ctx.wait(ctx.submit(d_frame, mp, d_mask, d_clean))
         mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]

@@ -214,9 +214,10 @@ static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
 }
 
 // Gain estimation (frames with gain 0) at level k: the pair-sum passes, then
-// the N table where the gain changed.  Two CTAs per SM per frame.
+// the N table where the gain changed.  Four CTAs per SM per frame (the
+// pass kernel is bounded to 64 registers for four resident CTAs).
 static void launch_gain_level(const FrameDesc* ddesc, int nf, int k, int num_sms, cudaStream_t s) {
-  const dim3 grid((unsigned)(2 * num_sms), (unsigned)nf);
+  const dim3 grid((unsigned)(4 * num_sms), (unsigned)nf);
   for (int r = 0; r < kGainPasses; ++r) gain_pass_kernel<<<grid, NT, 0, s>>>(ddesc, nf, k, r);
   ntab_level_kernel<<<dim3(256, (unsigned)nf), 256, 0, s>>>(ddesc, nf, k);
 }

@@ -433,7 +433,7 @@ __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
 // last block is the one whose arrival completes the count.  Every block of
 // a frame takes the same early exit, since it reads only what earlier
 // launches wrote.
-__global__ void __launch_bounds__(NT) gain_pass_kernel(const FrameDesc* __restrict__ fr, int nframes, int k,
+__global__ void __launch_bounds__(NT, 4) gain_pass_kernel(const FrameDesc* __restrict__ fr, int nframes, int k,
                                                        int r) {
   const int fi = blockIdx.y;
   if (fi >= nframes) return;
