@@ -178,6 +178,7 @@ def test_argument_errors(ctx):
     f = lacos.to_device(noisy_with_hits(16, 16, seed=1))
     m = torch.empty((16, 16), dtype=torch.uint8, device="cuda")
     c = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    # f is float32: gain 0 (estimate the gain) is for uint16 frames only
     for bad in (dict(gain=0.0), dict(gain=-1.0), dict(sigclip=0.0), dict(niter=-1), dict(niter=257),
                 dict(readnoise=-1.0), dict(objlim=float("nan")), dict(satgrow=-1), dict(satgrow=5)):
         kw = dict(gain=1.0, readnoise=1.5)
