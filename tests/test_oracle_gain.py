@@ -71,6 +71,35 @@ def test_clipping_boundary_is_inclusive_and_exact():
     assert g is None  # the survivors are all equal: V = 0
 
 
+def test_gain_closed_forms():
+    # Pairs (1, 0) and (0, 1), rn = 1: n = 2, d = +-1, V = 2, A = 2, so
+    # 2 g^2 - 2 g - 2*2*1 = 0, i.e. (g - 2)(g + 1) = 0: g = 2 exactly.
+    I = np.array([[1, 0, 0, 1]], np.float32)
+    z = np.zeros(I.shape, np.uint8)
+    g, rounds, st = oracle.estimate_gain(I, z, z, 1.0)
+    assert st == (2, 0, 2, 2) and g == 2.0
+    # Without read noise g = A / V: four pairs 101/100 alternating, V = 4, A = 804.
+    I = np.array([[101, 100, 100, 101, 101, 100, 100, 101]], np.float32)
+    z = np.zeros(I.shape, np.uint8)
+    g, rounds, st = oracle.estimate_gain(I, z, z, 0.0)
+    assert st == (4, 0, 4, 804) and g == 201.0
+
+
+def test_clipping_stops_after_five_rounds():
+    # 100 zero differences and outliers 2, 10, 50, 250, 1250, 6250, 31250
+    # (ratio 5): in each round the largest survivor dominates the variance,
+    # sigma ~ a_max / sqrt(n) ~ a_max / 10, so it alone lies beyond 3 sigma
+    # (~0.3 a_max) while the next one (a_max / 5) stays inside.  One outlier
+    # goes per round; after the fifth round {0 x 100, 2, 10} remain (n 102,
+    # sum 12, sum of squares 104), although a sixth and seventh round would
+    # still drop 10 and 2.
+    I, M = _pairs_image(np.array([0] * 100 + [2, 10, 50, 250, 1250, 6250, 31250]))
+    g, rounds, st = oracle.estimate_gain(I, M, np.zeros_like(M), 2.0)
+    assert rounds == 5
+    assert st == (102, 12, 104, 102 * 2000 + 12)
+    assert g is not None
+
+
 def _clip_variance_factor(rounds: int) -> float:
     """Variance of a unit normal after `rounds` progressive 3-sigma clips."""
     t, var = np.inf, 1.0
