@@ -68,3 +68,29 @@ def test_networks_header_matches_generator_and_verifies():
     text = open(os.path.join(ROOT, "paper_2602_17938_gb300", "csrc", "networks.cuh")).read()
     for name, (dag, outs, shape, doc) in nets.items():
         assert gen.emit_function(name, dag, outs, shape, doc) in text, name
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    # The ctypes mirrors in the binding must have the header's sizes and field
+    # offsets: a C program built against include/lacos.h prints them.
+    import subprocess
+    from paper_2602_17938_gb300 import lacos
+    structs = {"lacos_params": lacos.Params, "lacos_result": lacos.Result, "lacos_profile": lacos.Profile}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lacos.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
