@@ -11,7 +11,7 @@
 // compact objects, neighbour inclusion, median replacement), with the three
 // user parameters of "Main parameters" (objlim, sigfrac, sigclip) plus gain
 // and read noise.  The paper does not restate the equations; the readings
-// taken here (numbered C1..C15) are listed in the design notes and repeated
+// taken here (numbered C1..C17) are listed in the design notes and repeated
 // next to each step below.
 //
 // Every function is templated on the working type T (float or double).  For
