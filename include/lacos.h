@@ -241,7 +241,8 @@ size_t lacos_scratch_bytes(int ny, int nx);
 /* Last CUDA error code seen by the context (0 if none). */
 int lacos_last_cuda_error(lacos_ctx *c);
 
-/* Library version string. */
+/* Library version string, "lacos-gb300 <major>.<minor> (sm_103a)"; the number
+ * changes with the ABI (0.2: lacos_result.gain, LACOS_ENOGAIN, gain = 0). */
 const char *lacos_version(void);
 
 /* Self-check of the division the uint16 path uses instead of IEEE division

@@ -540,7 +540,7 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
 
 extern "C" {
 
-const char* lacos_version(void) { return "lacos-gb300 0.1 (sm_103a)"; }
+const char* lacos_version(void) { return "lacos-gb300 0.2 (sm_103a)"; }
 
 int lacos_selftest_division(float gain, float readnoise, unsigned long long* mismatches) {
   if (!mismatches || !(gain > 0.0f) || !(readnoise >= 0.0f) || !std::isfinite(gain) || !std::isfinite(readnoise))
