@@ -167,8 +167,8 @@ int lacos_wait(lacos_ctx *c, unsigned long long ticket, lacos_result *res);
 /* Batched form: n frames of any sizes and dtypes processed together, one
  * launch per iteration level over a shared tile work queue (and a CUDA
  * graph replayed when the same batch is submitted again with
- * reuse_graph != 0).  Arrays have n entries; params may differ per frame
- * (niter included).  One ticket covers the whole batch; its lacos_result
+ * reuse_graph != 0).  1 <= n <= 65535.  Arrays have n entries; params may
+ * differ per frame (niter included).  One ticket covers the whole batch; its lacos_result
  * sums n_flagged and reports the largest iters_run; per-frame results go
  * to per_frame (host array of n, may be NULL) when the batch is polled. */
 int lacos_submit_batch(lacos_ctx *c, int n, const void *const *d_frames, const int *dtypes,

@@ -617,7 +617,8 @@ int lacos_submit_batch(lacos_ctx* c, int n, const void* const* d_frames, const i
                        const int* ny, const int* nx, const lacos_params* params,
                        uint8_t* const* d_masks, float* const* d_cleans, lacos_stream stream,
                        int reuse_graph, lacos_result* per_frame, unsigned long long* ticket) {
-  if (n < 1 || !d_frames || !dtypes || !ny || !nx || !params || !d_masks || !d_cleans)
+  // Per-frame kernels put the frames on the grid's y dimension (at most 65535).
+  if (n < 1 || n > 65535 || !d_frames || !dtypes || !ny || !nx || !params || !d_masks || !d_cleans)
     return LACOS_EINVAL;
   std::vector<FrameReq> fr((size_t)n);
   for (int i = 0; i < n; ++i)
