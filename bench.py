@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small profiling case (every kernel of the library once per level) and exit")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serving sweep at 1.1, 2, 4, 8, 16, 32 frames/s and saturation, "
+                         "500 requests each (about 15 minutes)")
     return ap.parse_args()
 
 
@@ -153,122 +158,245 @@ def oracle_sample(frame, spec, seconds_target=12.0, crop=256):
                       f"single-threaded float32 C++ oracle, {t_total:.1f} s"}
 
 
+def _oracle_crop(job):
+    """Worker: the float32 oracle on one crop (spawned process)."""
+    crop, gain, rn, satlevel, sigclip, sigfrac, objlim, niter = job
+    import oracle
+    oracle.run(crop, gain, rn, satlevel, sigclip, sigfrac, objlim, niter)
+    return crop.size
+
+
+def oracle_pool(cores: int):
+    """A pool of `cores` spawned processes (spawned, so that it may start after
+    CUDA is initialised) with the oracle built and loaded in each."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_warm, range(cores))
+    return pool
+
+
+def _oracle_warm(_):
+    import oracle
+    oracle._load()
+    return 0
+
+
+def oracle_sample_nproc(jobs, cores=None):
+    """Time the float32 oracle on every host core at once: one crop per process
+    at a time (frame-parallel, the oracle itself unchanged).  Returns the
+    aggregate Mpix/s over the wall time of all jobs."""
+    cores = cores or os.cpu_count() or 1
+    pool = oracle_pool(cores)
+    try:
+        t0 = time.perf_counter()
+        px = sum(pool.map(_oracle_crop, jobs, chunksize=1))
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return px / 1e6 / dt, dt, cores
+
+
+def crop_jobs(frame, spec, n, crop, rng):
+    ny, nx = frame.shape
+    out = []
+    for _ in range(n):
+        y0, x0 = int(rng.integers(0, ny - crop + 1)), int(rng.integers(0, nx - crop + 1))
+        c = frame[y0:y0 + crop, x0:x0 + crop].copy()
+        out.append((c, spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac, spec.objlim,
+                    spec.niter))
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the float32 CPU oracle on the workload, on every host
+    core (one 256 x 256 crop of the 61-Mpx frame per core per step)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
     from paper_2602_17938_gb300 import synth
     spec = synth.config_specs(1)[0]
     frame = synth.make_frame(spec)
-    import numpy as np
-    import oracle
-    oracle.build()
-    crop = 192
+    crop = 256
+    cores = os.cpu_count() or 1
     rng = np.random.default_rng(7)
-    ny, nx = frame.shape
-
-    def step():
-        y0, x0 = int(rng.integers(0, ny - crop)), int(rng.integers(0, nx - crop))
-        c = np.ascontiguousarray(frame[y0:y0 + crop, x0:x0 + crop])
-        oracle.run(c, spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac,
-                   spec.objlim, spec.niter)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    v = args.steps * crop * crop / 1e6 / dt
+    pool = oracle_pool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.map(_oracle_crop, crop_jobs(frame, spec, cores, crop, rng), chunksize=1)
+        jobs = [crop_jobs(frame, spec, cores, crop, rng) for _ in range(args.steps)]
+        t0 = time.perf_counter()
+        for j in jobs:
+            pool.map(_oracle_crop, j, chunksize=1)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    v = args.steps * cores * crop * crop / 1e6 / dt
+    sample = (f"per step one {crop}x{crop} crop of the workload frame on each of {cores} host cores "
+              "(spawned processes), niter=4, float32 C++ oracle")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{crop}x{crop} crop per step",
+            "config": {"workload": WORKLOAD, "sample": f"{cores} crops of {crop}x{crop} per step",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one {crop}x{crop} crop of the workload frame per step, "
-                                       "niter=4, single-threaded float32 C++ oracle"},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------ batched and served ---
-def run_batched(args, dev):
+def _time_passes(fn, steps, stream):
+    """Mean ms of `fn()` over `steps` passes, CUDA events on `stream` (after one warm-up pass)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def same_frames_legs(ctx, d_frames, params, masks, cleans, steps, stream):
+    """The same frames three ways on one context: one request per frame on the
+    caller's stream (lacos_submit, the plain path), one request per frame on
+    the slots' own streams so they overlap (lacos_submit_async), and one
+    batched request (lacos_submit_batch, a launch per level over a shared tile
+    queue, replayed from its CUDA graph).  Returns mean ms per pass of each."""
+    import torch
+
+    def plain():
+        ts = [ctx.submit(f, p, m, c, stream) for f, p, m, c in zip(d_frames, params, masks, cleans)]
+        for t in ts:
+            ctx.wait(t)
+
+    def overlapped():
+        ts = [ctx.submit_async(f, p, m, c) for f, p, m, c in zip(d_frames, params, masks, cleans)]
+        for t in ts:
+            ctx.wait(t)
+        torch.cuda.synchronize()
+
+    def batched():
+        t, _ = ctx.submit_batch(d_frames, params, masks, cleans, stream=stream, reuse_graph=True)
+        ctx.wait(t)
+
+    # overlapped(): completion is waited for on the host (the slots' streams
+    # are not the timing stream), so its events bracket host-side waits too.
+    return {"plain_ms": _time_passes(plain, steps, stream),
+            "overlapped_ms": _time_passes(overlapped, steps, stream),
+            "batched_ms": _time_passes(batched, steps, stream)}
+
+
+def run_batched(args, dev, cpu_cores=None):
     """64 frames of uneven sizes (2048^2 f32, 4096x3072 u16, 9576x6388 u16; the
     config-1 recipe with per-frame gain and read noise) in one request: one
-    launch per iteration level over a shared tile queue, replayed as a CUDA graph."""
+    launch per iteration level over a shared tile queue, replayed as a CUDA graph;
+    beside it the same 64 frames one request each, plain and overlapped.  Then
+    the same comparison on eight frames of the 61-Mpx recipe (its cosmic-ray
+    density, so that tile skipping is alike in all three forms).  Also cuts
+    crops of the 64 frames for the oracle's all-core timing."""
+    import numpy as np
     import torch
     from paper_2602_17938_gb300 import lacos, synth
-    specs = synth.config_specs(2)
-    t0 = time.perf_counter()
-    frames = synth.make_frames_parallel(specs)
-    gen_s = time.perf_counter() - t0
-    d_frames = [lacos.to_device(f, dev) for f in frames]
-    del frames
-    masks = [torch.empty(f.shape, dtype=torch.uint8, device=dev) for f in d_frames]
-    cleans = [torch.empty(f.shape, dtype=torch.float32, device=dev) for f in d_frames]
-    params = [lacos.make_params(sp.gain, sp.readnoise, sp.satlevel, sp.sigclip, sp.sigfrac,
-                                sp.objlim, sp.niter) for sp in specs]
-    npix = sum(sp.npix for sp in specs)
-    ctx = lacos.Context(dev.index or 0, hbm_budget_bytes=96 << 30, max_slots=2)
     stream = torch.cuda.current_stream(dev)
-    t, _ = ctx.submit_batch(d_frames, params, masks, cleans, reuse_graph=True)  # capture
-    ctx.wait(t)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.batched_steps)]
-    flagged = 0
-    for a, b in ev:
-        a.record(stream)
-        t, per = ctx.submit_batch(d_frames, params, masks, cleans, reuse_graph=True)
-        b.record(stream)
-        r = ctx.wait(t)
-        flagged = r.n_flagged
-    torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    ctx.close()
-    del d_frames, masks, cleans
-    torch.cuda.empty_cache()
-    return {"workload": "64 frames: 16x 2048x2048 f32, 16x 4096x3072 u16, 32x 9576x6388 u16 "
-                        "(seed 2), niter=4, one request, CUDA-graph replay",
-            "mpix_per_s": npix / 1e6 / (sum(ms) / 1e3 / len(ms)), "ms_per_batch": sum(ms) / len(ms),
-            "mpix_per_batch": npix / 1e6, "steps": len(ms), "n_flagged": flagged,
-            "frame_generation_s": gen_s, "l2": "inputs (4.6 GB) far exceed L2"}
+    out = {}
+    for name, specs in (("mixed64", synth.config_specs(2)),
+                        ("dense8", [synth.FrameSpec(**{**synth.config_specs(1)[0].__dict__, "seed": (1, i)})
+                                    for i in range(8)])):
+        t0 = time.perf_counter()
+        frames = synth.make_frames_parallel(specs)
+        gen_s = time.perf_counter() - t0
+        if name == "mixed64" and cpu_cores is not None:
+            rng = np.random.default_rng(2)
+            jobs = []
+            for f, sp in zip(frames, specs):
+                jobs += crop_jobs(f, sp, 2, 512, rng)
+            out["_oracle_jobs"] = jobs
+        d_frames = [lacos.to_device(f, dev) for f in frames]
+        del frames
+        masks = [torch.empty(f.shape, dtype=torch.uint8, device=dev) for f in d_frames]
+        cleans = [torch.empty(f.shape, dtype=torch.float32, device=dev) for f in d_frames]
+        params = [lacos.make_params(sp.gain, sp.readnoise, sp.satlevel, sp.sigclip, sp.sigfrac,
+                                    sp.objlim, sp.niter) for sp in specs]
+        npix = sum(sp.npix for sp in specs)
+        ctx = lacos.Context(dev.index or 0, hbm_budget_bytes=96 << 30, max_slots=len(specs) + 1)
+        legs = same_frames_legs(ctx, d_frames, params, masks, cleans, args.batched_steps, stream)
+        t, per = ctx.submit_batch(d_frames, params, masks, cleans, stream=stream, reuse_graph=True)
+        flagged = ctx.wait(t).n_flagged
+        ctx.close()
+        del d_frames, masks, cleans
+        torch.cuda.empty_cache()
+        mp = lambda ms: npix / 1e6 / (ms / 1e3)
+        out[name] = {"frames": len(specs), "mpix_per_pass": npix / 1e6, "steps": args.batched_steps,
+                     "n_flagged": flagged, "frame_generation_s": gen_s,
+                     "batched_mpix_per_s": mp(legs["batched_ms"]),
+                     "plain_same_frames_mpix_per_s": mp(legs["plain_ms"]),
+                     "overlapped_same_frames_mpix_per_s": mp(legs["overlapped_ms"]),
+                     **legs}
+    out["mixed64"]["workload"] = ("64 frames: 16x 2048x2048 f32, 16x 4096x3072 u16, 32x 9576x6388 u16 "
+                                  "(seed 2, 200 tracks per 512^2), niter=4")
+    out["dense8"]["workload"] = ("8 frames of the 9576x6388 u16 recipe (seeds (1, 0..7): 150000 tracks, "
+                                 "0.5% salt-and-pepper), niter=4")
+    out["l2"] = "inputs (1-4.6 GB) far exceed L2"
+    return out
+
+
+SERVING_POINTS = ((32.0, 500), (16.0, 500), (8.0, 200), (1.1, 30), (math.inf, 500))
+SERVING_POINTS_FULL = ((1.1, 500), (2.0, 500), (4.0, 500), (8.0, 500), (16.0, 500), (32.0, 500),
+                       (math.inf, 500))
 
 
 def run_serving(args, dev):
     """Poisson stream of 9576x6388 u16 frames with 10% 2048x2048 f32 frames,
-    admitted by a 120 GB HBM budget, requests overlapping on the device."""
-    import math
+    admitted by a 120 GB HBM budget, requests overlapping on the device.  The
+    requests cycle through 24 distinct frames (21 of 61 Mpx, 3 of 4 Mpx)."""
     import torch
     from paper_2602_17938_gb300 import lacos, serve, synth
-    specs = synth.config_specs(3, count=200)
-    big = [sp for sp in specs if sp.ny == 6388][:4]
-    small = [sp for sp in specs if sp.ny == 2048][:2]
-    pool_specs = big + small
-    pool = [lacos.to_device(f, dev) for f in synth.make_frames_parallel(pool_specs)]
-    p = lacos.make_params(1.0, 1.5)
+    specs = synth.config_specs(3, count=400)
+    big = [sp for sp in specs if sp.ny == 6388][:21]
+    small = [sp for sp in specs if sp.ny == 2048][:3]
     kinds = [0 if sp.ny == 6388 else 1 for sp in specs]
+    t0 = time.perf_counter()
+    pool_big = [lacos.to_device(f, dev) for f in synth.make_frames_parallel(big)]
+    pool_small = [lacos.to_device(f, dev) for f in synth.make_frames_parallel(small)]
+    gen_s = time.perf_counter() - t0
+    p = lacos.make_params(1.0, 1.5)
     points = []
+    plan = SERVING_POINTS_FULL if args.serving_full else SERVING_POINTS
     with serve.Server(dev.index or 0, hbm_budget_bytes=120 << 30, max_slots=96) as srv:
         # Warm-up: every slot the sweep can use gets its stream and scratch.
-        srv.run([serve.Request(pool[i % 4], p, 0.0) for i in range(96)])
-        for rate, n in ((1.1, 12), (8.0, 48), (32.0, 120), (math.inf, 160)):
+        srv.run([serve.Request(pool_big[i % len(pool_big)], p, 0.0) for i in range(96)])
+        for rate, n in plan:
             arr = synth.poisson_arrivals(rate, n) if math.isfinite(rate) else [0.0] * n
-            reqs = []
+            reqs, nb, ns = [], 0, 0
             for i in range(n):
-                fr = pool[i % 4] if kinds[i % len(kinds)] == 0 else pool[4 + i % 2]
+                if kinds[i % len(kinds)] == 0:
+                    fr, nb = pool_big[nb % len(pool_big)], nb + 1
+                else:
+                    fr, ns = pool_small[ns % len(pool_small)], ns + 1
                 reqs.append(serve.Request(fr, p, float(arr[i] - arr[0])))
             st = srv.run(reqs)
-            points.append({"rate_hz": rate if math.isfinite(rate) else "saturation", "requests": n,
+            points.append({"rate_hz": rate if math.isfinite(rate) else "saturation", "requests": st.n,
                            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
-                           "mpix_per_s": st.mpix_per_s, "max_in_flight": st.max_in_flight})
-    del pool
+                           "max_ms": max(r.latency for r in st.records) * 1e3,
+                           "mpix_per_s": st.mpix_per_s, "max_in_flight": st.max_in_flight,
+                           "makespan_s": st.makespan_s})
+    del pool_big, pool_small
     torch.cuda.empty_cache()
     return {"workload": "Poisson arrivals of 9576x6388 u16 frames, 10% 2048x2048 f32 (seed 3); "
-                        "6 distinct frames reused round-robin; 120 GB HBM budget; lacos_submit_async",
-            "points": points}
+                        "24 distinct device-resident frames (21 large, 3 small) cycled; 120 GB HBM budget; "
+                        "lacos_submit_async",
+            "percentiles": "nearest rank over the point's requests (p99 of 500 is the 6th largest)",
+            "frame_generation_s": gen_s, "points": points}
 
 
 # ------------------------------------------------------------- GPU arm -----
@@ -374,12 +502,19 @@ def run_ours(args):
                   for name in ("core", "grow")}
     per_kernel["final"] = sum(p["final_ms"] for p in profs)
     n_launch = len(det_ms)
-    ops = sum(netcost.detect_minmax_ops(p) for p in profs)
     det_avg_ms = sum(det_ms) / max(1, n_launch)
-    achieved = ops / n_launch / (det_avg_ms * 1e-3) / 1e12 if n_launch else None
+    # Algorithmic min/max work of the core launches in INSTRUCTIONS: the dense
+    # networks run on packed u16x2 pairs for this uint16 frame (one instruction,
+    # two outputs), S' and F on single lanes.  The ALU pipe issues min/max at
+    # the same measured instruction rate for f32 and u16x2 operands, so that
+    # rate is the peak; frac = achieved / peak = ideal time / measured time.
+    works = [netcost.detect_work(p, packed=True) for p in profs]
+    instr = sum(w["instr"] for w in works)
+    achieved = instr / n_launch / (det_avg_ms * 1e-3) / 1e12 if n_launch else None
     peak_f32, peak_u16 = alu_peak()
-    peak = peak_f32 / 1e3 if peak_f32 else None
+    peak = min(peak_f32, peak_u16) / 1e3 if (peak_f32 and peak_u16) else None
     share = per_kernel["core"] / sum(per_kernel.values())
+    by_kind = {k: sum(w[k] for w in works) / len(works) for k in ("dense_instr", "sprime_instr", "fine_instr")}
     # End to end through the public API: lacos_submit_host copies the pinned
     # host frame in and the mask and cleaned frame out inside every step;
     # E2E_DEPTH requests in flight overlap one step's upload, another's
@@ -410,12 +545,20 @@ def run_ours(args):
     torch.cuda.empty_cache()
     batched = serving = None
     if ws == 1 and not args.no_batched:
-        batched = run_batched(args, dev)
+        batched = run_batched(args, dev, cpu_cores=None if args.no_cpu_baseline else os.cpu_count())
     if ws == 1 and not args.no_serving:
         serving = run_serving(args, dev)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else oracle_sample(frame, spec)
+    cpu_nproc = None
+    if batched and "_oracle_jobs" in batched:
+        jobs = batched.pop("_oracle_jobs")
+        v, dt, cores = oracle_sample_nproc(jobs)
+        cpu_nproc = {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                     "sample": f"{len(jobs)} crops of {jobs[0][0].shape[0]}x{jobs[0][0].shape[1]} px, two from "
+                               f"each of the 64 mixed-batch frames, one crop per process on {cores} host cores "
+                               f"(frame-parallel, float32 C++ oracle unchanged), niter=4, {dt:.1f} s wall"}
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps,
@@ -424,11 +567,18 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "ny": ny, "nx": nx, "frame_dtype": "u16", "niter": spec.niter,
                    "frames_per_call": 1, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tminmax/s",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "T min/max instructions/s",
                      "frac": (achieved / peak) if (achieved and peak) else None,
                      "traffic": NCU_CORE_TRAFFIC.get(kernel_source_sha()),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
-                     "kernel": "core_kernel", "peak_source": "measured min.f32/max.f32 issue rate",
+                     "kernel": "core_kernel",
+                     "peak_source": "measured: min/max issue rate of the ALU pipe (csrc/alu_peak.cu), "
+                                    "the lower of its f32 and u16x2 figures",
+                     "work": "per step: dense med5+med3 networks at computed tile pixels (packed u16x2, "
+                             "half an instruction per output-op) + med5 at S' items + med7 at F items",
+                     "work_instr_per_step": by_kind,
+                     "ideal_ms_per_step": (sum(by_kind.values()) / (peak * 1e12) * 1e3) if peak else None,
                      "avg_launch_ms": det_avg_ms, "launch_share": share,
                      "kernel_ms_per_step": {k: v / len(profs) for k, v in per_kernel.items()}},
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": 2 * npix,
@@ -447,17 +597,47 @@ def run_ours(args):
         line["batched"] = batched
     if serving:
         line["serving"] = serving
-        sat = serving["points"][0]
-        line["p99_latency_ms"] = sat["p99_ms"]
-        line["p99_latency_at"] = f"{sat['rate_hz']} frames/s Poisson, 120 GB budget"
+        head = next(pt for pt in serving["points"] if pt["rate_hz"] != "saturation" and pt["requests"] >= 500)
+        line["p99_latency_ms"] = head["p99_ms"]
+        line["p99_latency_at"] = (f"{head['rate_hz']} frames/s Poisson, {head['requests']} requests, "
+                                  "120 GB budget")
     if cpu:
         line["cpu_baseline"] = cpu
+    if cpu_nproc:
+        line["cpu_baseline_nproc"] = cpu_nproc
     print(json.dumps(line), flush=True)
+
+
+def run_profile_case():
+    """The case the per-kernel ncu summaries are taken on: a 9576 x 8000 uint16
+    frame of the 61-Mpx recipe (153 MB, more than L2), cleaned twice through the
+    C ABI -- default parameters (ntab, core, grow, finalize kernels), then with
+    the gain estimated and saturated-star protection (satseed, satgrow,
+    gain_pass, ntab_level kernels) -- at niter=4."""
+    import torch
+    from paper_2602_17938_gb300 import lacos, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    spec = synth.FrameSpec(**{**synth.config_specs(1)[0].__dict__, "ny": 8000, "seed": (1, 100),
+                              "n_stars": 5000, "n_tracks": 188000})
+    frame = synth.make_frame(spec)
+    d = lacos.to_device(frame)
+    m = torch.empty(frame.shape, dtype=torch.uint8, device="cuda")
+    c = torch.empty(frame.shape, dtype=torch.float32, device="cuda")
+    with lacos.Context(0) as ctx:
+        for kw in (dict(), dict(gain=0.0, satgrow=2)):
+            p = lacos.make_params(**{**dict(gain=spec.gain, readnoise=spec.readnoise, niter=4), **kw})
+            r = ctx.wait(ctx.submit(d, p, m, c))
+            print(json.dumps({"profile_case": kw, "status": r.status, "iters_run": r.iters_run,
+                              "n_flagged": r.n_flagged, "gain": r.gain}), flush=True)
+    torch.cuda.synchronize()
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

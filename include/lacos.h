@@ -26,8 +26,9 @@
  *
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
- * its scratch (5 bits per pixel, plus 512 KiB and 3 bytes per 32x64 tile
- * per frame), charged against the context's HBM budget.
+ * its scratch (5 bits per pixel, 6 with satgrow > 0, plus 512 KiB and 3
+ * bytes per 32x64 tile per frame; lacos_request_bytes gives the figure),
+ * charged against the context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
  * are the LACOS_E* codes below; lacos_poll also returns LACOS_PENDING (1).
@@ -205,11 +206,14 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
  * device allocator.  The scratch lives in a fixed array of
  * LACOS_STATIC_SCRATCH_BYTES inside this library's device image, held by
  * every GPU that loads the library until the process exits; frames whose
- * scratch (lacos_scratch_bytes(ny, nx)) exceeds it -- above about 106 Mpx,
- * e.g. 9576 x 6388 fits, 12000 x 12000 does not -- are rejected with
- * LACOS_ENOMEM.  Arguments, layout and results are those of lacos_submit
- * (outputs written to the caller's d_mask and d_clean); the call queues the
- * work on `stream`, waits for it and fills *res (may be NULL).  The first
+ * scratch (lacos_request_bytes(ny, nx, p)) exceeds it are rejected with
+ * LACOS_ENOMEM: above about 106 Mpx with satgrow = 0 (five bit-planes;
+ * 9576 x 6388 fits, 12000 x 12000 does not), above about 88 Mpx with
+ * satgrow > 0 (a sixth plane holds the grown saturated set).  Arguments,
+ * layout and results are those of lacos_submit (outputs written to the
+ * caller's d_mask and d_clean), except res->latency_ms: the host time from
+ * entry to return, since the call queues the work on `stream`, waits for it
+ * and then fills *res (may be NULL).  The first
  * call on a device looks up the array's device address and the launch
  * geometry for that device (no allocation); make that first call before
  * any stream capture.  All calls share the one array and it keeps the last
@@ -220,12 +224,19 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
 int lacos_run_static(const void *d_frame, lacos_dtype dt, int ny, int nx, const lacos_params *p,
                      uint8_t *d_mask, float *d_clean, lacos_stream stream, lacos_result *res);
 
-/* Core-kernel variant of the context (0..3: register allocation bounded for
- * 1..4 resident CTAs per SM; more CTAs hide more latency, fewer registers
- * spill more).  lacos_autotune runs the given frame `reps` times (after one
- * warm-up) with each variant, keeps the fastest, and reports each variant's
- * mean device time in variant_ms[4] (may be NULL).  Results do not depend
- * on the variant. */
+/* Core-kernel variant of the context: the tile shape of the detection
+ * kernel and the resident CTAs per SM its registers are bounded for.
+ *   0..3: 32 x 64 tiles, 256 threads, 1..4 CTAs per SM (more CTAs hide more
+ *         latency, fewer registers spill more; 3 is the default);
+ *   4, 5: 64 x 64 tiles, 512 threads, 1 or 2 CTAs per SM;
+ *   6, 7: 32 x 128 tiles, 512 threads, 1 or 2 CTAs per SM.
+ * Larger tiles recompute less of the halo (each tile evaluates its medians
+ * up to 6 pixels beyond its edges) but hold more shared memory per CTA.
+ * lacos_autotune runs the given frame `reps` times (after one warm-up) with
+ * each variant, keeps the fastest, and reports each variant's mean device
+ * time in variant_ms[LACOS_CORE_VARIANTS] (may be NULL).  Results do not
+ * depend on the variant. */
+#define LACOS_CORE_VARIANTS 8
 int lacos_set_core_variant(lacos_ctx *c, int variant);
 int lacos_get_core_variant(lacos_ctx *c, int *variant);
 int lacos_autotune(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int nx,
@@ -235,14 +246,21 @@ int lacos_autotune(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, in
 /* Drain in-flight work, free all library memory and the context. */
 int lacos_destroy(lacos_ctx *c);
 
-/* Scratch bytes a frame of ny x nx needs (what the budget is charged). */
+/* Scratch bytes a frame of ny x nx needs with default parameters
+ * (satgrow = 0); what the budget is charged for such a request. */
 size_t lacos_scratch_bytes(int ny, int nx);
+
+/* Scratch bytes a request for one ny x nx frame with parameters *p (NULL:
+ * defaults) is charged against the budget; satgrow > 0 adds one bit-plane.
+ * 0 for empty extents. */
+size_t lacos_request_bytes(int ny, int nx, const lacos_params *p);
 
 /* Last CUDA error code seen by the context (0 if none). */
 int lacos_last_cuda_error(lacos_ctx *c);
 
 /* Library version string, "lacos-gb300 <major>.<minor> (sm_103a)"; the number
- * changes with the ABI (0.2: lacos_result.gain, LACOS_ENOGAIN, gain = 0). */
+ * changes with the ABI (0.2: lacos_result.gain, LACOS_ENOGAIN, gain = 0;
+ * 0.3: lacos_request_bytes). */
 const char *lacos_version(void);
 
 /* Self-check of the division the uint16 path uses instead of IEEE division

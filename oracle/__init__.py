@@ -44,8 +44,13 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            # LACOS_ORACLE_LIB: another build of this source (the planted-slip
+            # tests load mutated copies through it).
+            path = os.environ.get("LACOS_ORACLE_LIB")
+            if not path:
+                build()
+                path = _LIB
+            lib = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i, f, ll = ctypes.c_int, ctypes.c_float, ctypes.c_longlong
             for suf in ("f32", "f64"):

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -100,9 +101,10 @@ bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) 
 
 int wpr_of(int nx) { return (nx + 31) / 32; }
 size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
-// Per-tile level marks of the core kernel: two ping-pong bytes and a sticky one per tile.
+// Per-tile level marks of the core kernel: two ping-pong bytes and a sticky one per
+// tile, sized for the smallest core tile (32 x 64) so that every variant fits.
 size_t tflag_bytes(int ny, int nx) {
-  return align_up(3 * (size_t)((nx + TW - 1) / TW) * (size_t)((ny + TH - 1) / TH));
+  return align_up(3 * (size_t)((nx + G32x64::TW - 1) / G32x64::TW) * (size_t)((ny + G32x64::TH - 1) / G32x64::TH));
 }
 
 struct Layout {
@@ -129,6 +131,26 @@ Layout layout_for(const std::vector<FrameReq>& fr) {
 
 }  // namespace
 
+// Core-kernel variants: tile geometry (shape, threads per CTA) and the
+// resident CTAs per SM its register allocation is bounded for.  0..3 are the
+// 32 x 64 tiles at 1..4 CTAs per SM; the others trade more shared memory per
+// CTA (and fewer CTAs per SM) for less halo recomputation per pixel.
+using CoreFn = void (*)(const FrameDesc*, int, unsigned, unsigned, int, unsigned*);
+struct CoreVariant {
+  int th, tw, nt, minb;
+  CoreFn fn[2];    // by frame dtype (LACOS_F32, LACOS_U16)
+  size_t smem[2];  // dynamic shared memory per CTA, by frame dtype
+};
+template <class G, int MINB>
+constexpr CoreVariant make_variant() {
+  return {G::TH, G::TW, G::NT, MINB, {core_kernel<G, MINB, float>, core_kernel<G, MINB, uint16_t>},
+          {kCoreSmemBytes<G, float>, kCoreSmemBytes<G, uint16_t>}};
+}
+static const CoreVariant kCoreVariants[LACOS_CORE_VARIANTS] = {
+    make_variant<G32x64, 1>(), make_variant<G32x64, 2>(), make_variant<G32x64, 3>(), make_variant<G32x64, 4>(),
+    make_variant<G64x64, 1>(), make_variant<G64x64, 2>(), make_variant<G32x128, 1>(), make_variant<G32x128, 2>()};
+constexpr int kDefaultCoreVariant = 3;
+
 struct lacos_ctx {
   int device = 0;
   size_t budget = 0;
@@ -138,9 +160,8 @@ struct lacos_ctx {
   unsigned long long next_ticket = 1;
   std::atomic<int> last_cuda{0};
   int num_sms = 0;
-  int core_variant = 3;                 // index into kCoreVariants[dtype]
-  int blocks_per_sm_core_v[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};
-  int blocks_per_sm_core = 1;
+  int core_variant = kDefaultCoreVariant;  // index into kCoreVariants
+  int blocks_per_sm_core_v[2][LACOS_CORE_VARIANTS] = {};  // resident CTAs by dtype and variant
   int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
@@ -151,13 +172,6 @@ struct lacos_ctx {
 // times the resident core CTAs.
 constexpr unsigned kChainWaves = 8;
 
-using CoreFn = void (*)(const FrameDesc*, int, unsigned, unsigned, int, unsigned*);
-// Core-kernel variants by frame dtype (LACOS_F32, LACOS_U16): register
-// allocation bounded for 1, 2, 3 or 4 CTAs/SM.
-static const CoreFn kCoreVariants[2][4] = {
-    {core_kernel<1, float>, core_kernel<2, float>, core_kernel<3, float>, core_kernel<4, float>},
-    {core_kernel<1, uint16_t>, core_kernel<2, uint16_t>, core_kernel<3, uint16_t>, core_kernel<4, uint16_t>}};
-static const size_t kCoreSmem[2] = {kCoreSmemBytes<float>, kCoreSmemBytes<uint16_t>};
 
 static int cuda_fail(lacos_ctx* c, cudaError_t e) {
   if (c) c->last_cuda = (int)e;
@@ -218,7 +232,7 @@ static void evict_idle(lacos_ctx* c, size_t need, cudaStream_t s) {
 // pass kernel is bounded to 64 registers for four resident CTAs).
 static void launch_gain_level(const FrameDesc* ddesc, int nf, int k, int num_sms, cudaStream_t s) {
   const dim3 grid((unsigned)(4 * num_sms), (unsigned)nf);
-  for (int r = 0; r < kGainPasses; ++r) gain_pass_kernel<<<grid, NT, 0, s>>>(ddesc, nf, k, r);
+  for (int r = 0; r < kGainPasses; ++r) gain_pass_kernel<<<grid, kBlock, 0, s>>>(ddesc, nf, k, r);
   ntab_level_kernel<<<dim3(256, (unsigned)nf), 256, 0, s>>>(ddesc, nf, k);
 }
 
@@ -229,12 +243,14 @@ static void launch_gain_level(const FrameDesc* ddesc, int nf, int k, int num_sms
 static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, const Layout& L,
                    cudaStream_t s, bool prof, cudaEvent_t chain = nullptr) {
   char* d = (char*)sl.dscratch;
+  const int cv = c->core_variant;
+  const CoreVariant& V = kCoreVariants[cv];
   unsigned* heads = (unsigned*)(d + L.heads);
   FrameDesc* ddesc = (FrameDesc*)(d + L.descs);
   FrameState* dstate = (FrameState*)(d + L.states);
   // Host descriptors in the pinned buffer (states come back after them).
   FrameDesc* hdesc = (FrameDesc*)sl.hpinned;
-  unsigned total = 0;
+  unsigned total = 0, total_fin = 0;
   unsigned long long total_words = 0;
   unsigned total_gblk = 0;
   int max_niter = 0;
@@ -288,12 +304,18 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     h.fnorm = f.p.fine_norm;
     h.satgrow = f.p.satgrow;
     h.sepmed = f.p.sepmed;
-    h.tiles_x = (f.nx + TW - 1) / TW;
-    const unsigned tiles = (unsigned)h.tiles_x * (unsigned)((f.ny + TH - 1) / TH);
+    h.th = V.th;
+    h.tw = V.tw;
+    h.tiles_x = (f.nx + V.tw - 1) / V.tw;
+    const unsigned tiles = (unsigned)h.tiles_x * (unsigned)((f.ny + V.th - 1) / V.th);
     h.tile_begin = total;
     total += tiles;
     h.tile_end = total;
     if (f.dtype == LACOS_U16) tiles_u16 = total;
+    h.ftiles_x = (f.nx + FG::TW - 1) / FG::TW;
+    h.fin_begin = total_fin;
+    total_fin += (unsigned)h.ftiles_x * (unsigned)((f.ny + FG::TH - 1) / FG::TH);
+    h.fin_end = total_fin;
     h.word_begin = total_words;
     total_words += (unsigned long long)f.ny * h.wpr;
     h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
@@ -310,14 +332,13 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     CK(cudaMemsetAsync(d + L.mask_off[i] + 5 * mb + kNtabBytes, 0, tflag_bytes(fr[i].ny, fr[i].nx), s));
   }
   const int nf = (int)fr.size();
-  const int cv = c->core_variant;
   // Core launches: [dtype] -> item range and grid.
   const unsigned rng[2][2] = {{tiles_u16, total}, {0, tiles_u16}};
   unsigned gdt[2];
   for (int dt = 0; dt < 2; ++dt)
     gdt[dt] = std::min<unsigned>(rng[dt][1] - rng[dt][0],
                                  (unsigned)(c->num_sms * c->blocks_per_sm_core_v[dt][cv]));
-  const unsigned gfi = std::min<unsigned>(total, (unsigned)(c->num_sms * c->blocks_per_sm_final));
+  const unsigned gfi = std::min<unsigned>(total_fin, (unsigned)(c->num_sms * c->blocks_per_sm_final));
   // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
   // [2n+1] after finalize.
   const int nev = 2 * max_niter + 2;
@@ -350,16 +371,16 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     }
     for (int dt : {1, 0}) {
       if (!gdt[dt]) continue;
-      kCoreVariants[dt][cv]<<<gdt[dt], NT, kCoreSmem[dt], s>>>(ddesc, nf, rng[dt][0], rng[dt][1], k,
-                                                                heads + kHeadCore + dt * kHeadLevels + k);
+      V.fn[dt]<<<gdt[dt], V.nt, V.smem[dt], s>>>(ddesc, nf, rng[dt][0], rng[dt][1], k,
+                                                  heads + kHeadCore + dt * kHeadLevels + k);
       CK(cudaGetLastError());
     }
     if (int rc = mark(2 * k - 1)) return rc;
-    grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, nf, total_gblk, k);
+    grow_kernel<<<total_gblk, kBlock, 0, s>>>(ddesc, nf, total_gblk, k);
     CK(cudaGetLastError());
     if (int rc = mark(2 * k)) return rc;
   }
-  finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, nf, total, heads + kHeadFinal);
+  finalize_kernel<<<gfi, kBlock, 0, s>>>(ddesc, nf, total_fin, heads + kHeadFinal);
   CK(cudaGetLastError());
   if (int rc = mark(2 * max_niter + 1)) return rc;
   if (chain) CK(cudaEventRecord(chain, s));
@@ -470,7 +491,8 @@ static int submit_impl(lacos_ctx* c, const std::vector<FrameReq>& fr_in, cudaStr
                          cudaMemcpyHostToDevice, s));
     bool chain = false;
     if (hio) {
-      const unsigned tiles = (unsigned)((fr[0].ny + TH - 1) / TH) * (unsigned)((fr[0].nx + TW - 1) / TW);
+      const CoreVariant& V = kCoreVariants[c->core_variant];
+      const unsigned tiles = (unsigned)((fr[0].ny + V.th - 1) / V.th) * (unsigned)((fr[0].nx + V.tw - 1) / V.tw);
       const unsigned resident = (unsigned)c->num_sms * (unsigned)c->blocks_per_sm_core_v[fr[0].dtype][c->core_variant];
       chain = tiles >= kChainWaves * resident;
     }
@@ -540,7 +562,7 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
 
 extern "C" {
 
-const char* lacos_version(void) { return "lacos-gb300 0.2 (sm_103a)"; }
+const char* lacos_version(void) { return "lacos-gb300 0.3 (sm_103a)"; }
 
 int lacos_selftest_division(float gain, float readnoise, unsigned long long* mismatches) {
   if (!mismatches || !(gain > 0.0f) || !(readnoise >= 0.0f) || !std::isfinite(gain) || !std::isfinite(readnoise))
@@ -567,8 +589,19 @@ int lacos_selftest_division(float gain, float readnoise, unsigned long long* mis
 size_t lacos_scratch_bytes(int ny, int nx) {
   if (ny < 1 || nx < 1) return 0;
   std::vector<FrameReq> fr(1);
+  std::memset(&fr[0], 0, sizeof(FrameReq));
   fr[0].ny = ny;
   fr[0].nx = nx;
+  return layout_for(fr).total;
+}
+
+size_t lacos_request_bytes(int ny, int nx, const lacos_params* p) {
+  if (ny < 1 || nx < 1) return 0;
+  std::vector<FrameReq> fr(1);
+  std::memset(&fr[0], 0, sizeof(FrameReq));
+  fr[0].ny = ny;
+  fr[0].nx = nx;
+  if (p) fr[0].p = *p;
   return layout_for(fr).total;
 }
 
@@ -582,20 +615,20 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   for (int dt = 0; dt < 2; ++dt)
-    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
-      e = cudaFuncSetAttribute(kCoreVariants[dt][v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kCoreSmem[dt]);
+    for (int v = 0; v < LACOS_CORE_VARIANTS && e == cudaSuccess; ++v) {
+      const CoreVariant& V = kCoreVariants[v];
+      e = cudaFuncSetAttribute(V.fn[dt], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem[dt]);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[dt][v], kCoreVariants[dt][v],
-                                                          NT, kCoreSmem[dt]);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_core_v[dt][v], V.fn[dt], V.nt,
+                                                          V.smem[dt]);
       c->blocks_per_sm_core_v[dt][v] = std::max(1, c->blocks_per_sm_core_v[dt][v]);
     }
   if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
     const int v = std::atoi(env);
-    if (v >= 0 && v < 4) c->core_variant = v;
+    if (v >= 0 && v < LACOS_CORE_VARIANTS) c->core_variant = v;
   }
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, NT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, kBlock, 0);
   if (e != cudaSuccess) {
     delete c;
     return LACOS_ECUDA;
@@ -645,7 +678,7 @@ int lacos_submit_host(lacos_ctx* c, const void* h_frame, lacos_dtype dt, int ny,
 }
 
 int lacos_set_core_variant(lacos_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 3) return LACOS_EINVAL;
+  if (!c || variant < 0 || variant >= LACOS_CORE_VARIANTS) return LACOS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->core_variant = variant;
   return LACOS_OK;
@@ -664,7 +697,7 @@ int lacos_autotune(lacos_ctx* c, const void* d_frame, lacos_dtype dt, int ny, in
   if (!c || !p || reps < 1) return LACOS_EINVAL;
   int best = -1;
   float best_ms = 0.0f;
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < LACOS_CORE_VARIANTS; ++v) {
     int rc = lacos_set_core_variant(c, v);
     if (rc) return rc;
     double sum = 0.0;
@@ -773,7 +806,7 @@ __device__ __align__(256) unsigned char g_static_scratch[LACOS_STATIC_SCRATCH_BY
 struct StaticDevice {
   bool ready = false;
   void* scratch = nullptr;  // device address of g_static_scratch on this device
-  int num_sms = 0, bpsm_core[2] = {1, 1}, bpsm_final = 1, core_variant = 3;
+  int num_sms = 0, bpsm_core[2] = {1, 1}, bpsm_final = 1, core_variant = kDefaultCoreVariant;
 };
 std::mutex g_static_mu;
 constexpr int kStaticMaxDevices = 64;
@@ -792,19 +825,18 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
     if (e != cudaSuccess) return e;
     if (const char* env = std::getenv("LACOS_CORE_VARIANT")) {
       const int v = std::atoi(env);
-      if (v >= 0 && v < 4) sd.core_variant = v;
+      if (v >= 0 && v < LACOS_CORE_VARIANTS) sd.core_variant = v;
     }
+    const CoreVariant& V = kCoreVariants[sd.core_variant];
     e = cudaDeviceGetAttribute(&sd.num_sms, cudaDevAttrMultiProcessorCount, dev);
     for (int dt = 0; dt < 2 && e == cudaSuccess; ++dt) {
-      e = cudaFuncSetAttribute(kCoreVariants[dt][sd.core_variant],
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmem[dt]);
+      e = cudaFuncSetAttribute(V.fn[dt], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem[dt]);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core[dt], kCoreVariants[dt][sd.core_variant],
-                                                          NT, kCoreSmem[dt]);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core[dt], V.fn[dt], V.nt, V.smem[dt]);
       sd.bpsm_core[dt] = std::max(1, sd.bpsm_core[dt]);
     }
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, NT, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, kBlock, 0);
     if (e != cudaSuccess) return e;
     sd.bpsm_final = std::max(1, sd.bpsm_final);
     sd.ready = true;
@@ -818,6 +850,7 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
 extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int nx,
                                 const lacos_params* p, uint8_t* d_mask, float* d_clean,
                                 lacos_stream stream, lacos_result* res) {
+  const auto t_call = std::chrono::steady_clock::now();
   if (!p) return LACOS_EINVAL;
   const FrameReq f{d_frame, (int)dt, ny, nx, *p, d_mask, d_clean};
   if (!frame_valid(f)) return LACOS_EINVAL;
@@ -874,10 +907,17 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   h.fnorm = p->fine_norm;
   h.satgrow = p->satgrow;
   h.sepmed = p->sepmed;
-  h.tiles_x = (nx + TW - 1) / TW;
-  const unsigned total = (unsigned)h.tiles_x * (unsigned)((ny + TH - 1) / TH);
+  const CoreVariant& V = kCoreVariants[sd->core_variant];
+  h.th = V.th;
+  h.tw = V.tw;
+  h.tiles_x = (nx + V.tw - 1) / V.tw;
+  const unsigned total = (unsigned)h.tiles_x * (unsigned)((ny + V.th - 1) / V.th);
   h.tile_begin = 0;
   h.tile_end = total;
+  h.ftiles_x = (nx + FG::TW - 1) / FG::TW;
+  const unsigned total_fin = (unsigned)h.ftiles_x * (unsigned)((ny + FG::TH - 1) / FG::TH);
+  h.fin_begin = 0;
+  h.fin_end = total_fin;
   h.word_begin = 0;
   h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
   h.gblk_begin = 0;
@@ -894,7 +934,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
     return LACOS_ECUDA;
   const int di = f.dtype == LACOS_U16 ? 1 : 0;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core[di]));
-  const unsigned gfi = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_final));
+  const unsigned gfi = std::min<unsigned>(total_fin, (unsigned)(sd->num_sms * sd->bpsm_final));
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   if (p->satgrow) {
     const unsigned nw = (unsigned)((size_t)ny * wpr_of(nx));
@@ -903,11 +943,10 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   }
   for (int k = 1; k <= p->niter; ++k) {
     if (h.gain_est) launch_gain_level(ddesc, 1, k, sd->num_sms, s);
-    kCoreVariants[di][sd->core_variant]<<<gd, NT, kCoreSmem[di], s>>>(ddesc, 1, 0, total, k,
-                                                                      heads + kHeadCore + di * kHeadLevels + k);
-    grow_kernel<<<total_gblk, NT, 0, s>>>(ddesc, 1, total_gblk, k);
+    V.fn[di]<<<gd, V.nt, V.smem[di], s>>>(ddesc, 1, 0, total, k, heads + kHeadCore + di * kHeadLevels + k);
+    grow_kernel<<<total_gblk, kBlock, 0, s>>>(ddesc, 1, total_gblk, k);
   }
-  finalize_kernel<<<gfi, NT, 0, s>>>(ddesc, 1, total, heads + kHeadFinal);
+  finalize_kernel<<<gfi, kBlock, 0, s>>>(ddesc, 1, total_fin, heads + kHeadFinal);
   if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;
   FrameState hs;
   if (cudaMemcpyAsync(&hs, dstate, sizeof(FrameState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -921,7 +960,10 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
     res->gain = h.gain_est ? hs.gain : p->gain;
     res->iters_run = hs.iters_run;
     res->n_flagged = (long long)hs.flagged;
-    res->latency_ms = 0.0;
+    // The call blocks until its work is done: its latency is the host time
+    // from entry to completion (queueing behind earlier work on `stream`
+    // included).
+    res->latency_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call).count();
   }
   return LACOS_OK;
 }

@@ -73,10 +73,36 @@ __device__ __forceinline__ U16x2 MX(U16x2 a, U16x2 b) {
 
 namespace lacos {
 
-constexpr int TH = 32;   // output tile rows
-constexpr int TW = 64;   // output tile columns (two 32-bit mask words per row)
-constexpr int TWW = TW / 32;
-constexpr int NT = 256;  // threads per CTA
+// Threads per CTA of the kernels other than the core kernel.
+constexpr int kBlock = 256;
+
+// Tile geometry of a core-kernel variant: TH x TW output pixels per tile, NT
+// threads per CTA.  Regions grown around the tile are Reg<H, C>: H rows and
+// C columns on each side, row-major in shared memory, idx(0, 0) the tile's
+// first pixel.  Staged input regions carry 8 extra columns on each side
+// (more than the 6 and 3 the stencils need) so that every staged row starts
+// on a 16-byte boundary of both the frame and shared memory.
+template <int TH_, int TW_, int NT_>
+struct Geo {
+  static constexpr int TH = TH_, TW = TW_, NT = NT_;
+  static constexpr int TWW = TW / 32;                      // mask words per tile row
+  static constexpr int MWORDS = (TW + 12 + 31) / 32 + 1;   // mask words spanning the staged columns
+  template <int H, int C = H>
+  struct Reg {
+    static constexpr int W = TW + 2 * C;
+    static constexpr int Hh = TH + 2 * H;
+    static constexpr int N = W * Hh;
+    __host__ __device__ static constexpr int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
+  };
+  using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
+  using XR3 = Reg<3, 8>;  // finalize
+  static_assert(TW % 64 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
+};
+// The variants' tile shapes.  Finalize always runs on 32 x 64 tiles.
+using G32x64 = Geo<32, 64, 256>;
+using G64x64 = Geo<64, 64, 512>;
+using G32x128 = Geo<32, 128, 512>;
+using FG = G32x64;
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -127,8 +153,11 @@ struct FrameDesc {
   int niter, fnorm;
   int satgrow;       // radius of the protected region around saturated pixels (0..4)
   int sepmed;        // 1: both 5x5 detection medians taken separably (comparison mode)
-  int tiles_x;
-  unsigned int tile_begin, tile_end;    // this frame's range in the flattened tile list
+  int th, tw;        // core tile shape of the request's core-kernel variant
+  int tiles_x;       // core tiles per row
+  unsigned int tile_begin, tile_end;    // this frame's range in the flattened core-tile list
+  int ftiles_x;                         // finalize tiles (32 x 64) per row
+  unsigned int fin_begin, fin_end;      // this frame's range in the flattened finalize-tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
   unsigned int gblk_begin, gblk_x;      // growth blocks: this frame's first, blocks per row
 };
@@ -191,27 +220,20 @@ __device__ float maskmed_wide(const FrameDesc& f, const uint32_t* M, int gy, int
   return load_x0(f, gy, gx, bad);  // unreachable: a frame always keeps an unflagged pixel
 }
 
-
-// The tile grown by H rows and C columns on each side, row-major in shared
-// memory; idx(0, 0) is the tile's first pixel.
-template <int H, int C = H>
-struct Reg {
-  static constexpr int W = TW + 2 * C;
-  static constexpr int Hh = TH + 2 * H;
-  static constexpr int N = W * Hh;
-  __host__ __device__ static constexpr int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
-};
-// Staged input regions: 8 extra columns on each side (more than the 6 and 3
-// the stencils need) so that every staged row starts on a 16-byte boundary
-// of both the frame and shared memory.
-using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
-using XR3 = Reg<3, 8>;  // finalize
-
 __device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsigned item) {
   int lo = 0, hi = nframes - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (fr[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int frame_of_fin(const FrameDesc* fr, int nframes, unsigned item) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].fin_begin <= item) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -326,16 +348,14 @@ __device__ __forceinline__ bool maskmed7(const XT* X, const uint8_t* Mb, int P, 
 
 // ---- core: steps 1-4 on a tile --------------------------------------------
 
-constexpr int MWORDS = (TW + 12 + 31) / 32 + 1;  // mask words spanning R6 columns
-
-
 // Stages X0 and the mask M (clamped coordinates) on region H of a tile:
 // X (Reg<H>-indexed floats), Mb (bytes), via the mask words of the rows.
-template <int H, class XT>
+template <class G, int H, class XT>
 __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t* M, int oy, int ox,
-                                              XT* X, uint8_t* Mb, uint32_t (*Mw)[MWORDS],
+                                              XT* X, uint8_t* Mb, uint32_t (*Mw)[G::MWORDS],
                                               bool& bad) {
-  using R = Reg<H, 8>;
+  constexpr int TH = G::TH, TW = G::TW, NT = G::NT, MWORDS = G::MWORDS;
+  using R = typename G::template Reg<H, 8>;
   constexpr int C = 8;
   const int ny = f.ny, nx = f.nx;
   const int w0 = clampi(ox - C, 0, nx - 1) >> 5;
@@ -433,7 +453,7 @@ __global__ void ntab_kernel(const FrameDesc* __restrict__ fr, int nframes) {
 // last block is the one whose arrival completes the count.  Every block of
 // a frame takes the same early exit, since it reads only what earlier
 // launches wrote.
-__global__ void __launch_bounds__(NT, 4) gain_pass_kernel(const FrameDesc* __restrict__ fr, int nframes, int k,
+__global__ void __launch_bounds__(kBlock, 4) gain_pass_kernel(const FrameDesc* __restrict__ fr, int nframes, int k,
                                                        int r) {
   const int fi = blockIdx.y;
   if (fi >= nframes) return;
@@ -454,7 +474,7 @@ __global__ void __launch_bounds__(NT, 4) gain_pass_kernel(const FrameDesc* __res
   const uint16_t* x0 = static_cast<const uint16_t*>(f.x0);
   unsigned long long n = 0, s2 = 0, a = 0;
   long long s1 = 0;
-  for (unsigned w = blockIdx.x * NT + threadIdx.x; w < nwords; w += gridDim.x * NT) {
+  for (unsigned w = blockIdx.x * kBlock + threadIdx.x; w < nwords; w += gridDim.x * kBlock) {
     const int y = (int)(w / (unsigned)f.wpr), xw = (int)(w % (unsigned)f.wpr) * 32;
     const int cnt = min(32, f.nx - xw);  // pixels of this word
     uint32_t bad = __ldg(Mprev + w);
@@ -500,7 +520,7 @@ __global__ void __launch_bounds__(NT, 4) gain_pass_kernel(const FrameDesc* __res
     s2 += __shfl_down_sync(0xffffffffu, s2, o);
     a += __shfl_down_sync(0xffffffffu, a, o);
   }
-  __shared__ unsigned long long red[NT / 32][4];
+  __shared__ unsigned long long red[kBlock / 32][4];
   __shared__ int s_last;
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5][0] = n;
@@ -511,7 +531,7 @@ __global__ void __launch_bounds__(NT, 4) gain_pass_kernel(const FrameDesc* __res
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int q = 0; q < NT / 32; ++q)
+    for (int q = 0; q < kBlock / 32; ++q)
       for (int i = 0; i < 4; ++i) t[i] += red[q][i];
     if (t[0])
       for (int i = 0; i < 4; ++i) atomicAdd(&st->gsum[r][i], t[i]);
@@ -699,50 +719,55 @@ __device__ __forceinline__ float lplus(float vc, float up, float dn, float lf, f
 }
 
 // Shared memory of one core tile, by working-image type.
-template <class XT> struct CoreSmemT;
-template <> struct CoreSmemT<float> {
-  float X[XR6::N];               // X0 on R6, then the working image I_{k-1} on R4
-  uint8_t Mb[XR6::N];            // M_{k-1} on R6
-  uint32_t Mw[TH + 12][MWORDS];  // M_{k-1} words of the R6 rows (clamped rows)
-  float S[Reg<2>::N];            // S on R2
-  float N[TH * TW];              // N on the tile
-  float M3[Reg<3>::N];           // med3(I) on R3
-  uint16_t list[Reg<4>::N];      // work lists: replacement on R4; then fine-structure
-                                 // items from the front and S'-only items from the back
-  uint8_t flags[TH * TW];        // bit3: saturated
-  uint32_t pw[3][TH][TWW];       // the tile's sig, lo and candidate bit-plane words
-  uint32_t Sw[TH][TWW];          // satgrow > 0: the tile's words of the grown saturated set
-  unsigned nlist, nlist2;        // list lengths (S'-only, fine-structure)
-  unsigned nfine;                // F evaluations of the tile
+template <class G, class XT> struct CoreSmemT;
+template <class G> struct CoreSmemT<G, float> {
+  using XR6 = typename G::XR6;
+  float X[XR6::N];                       // X0 on R6, then the working image I_{k-1} on R4
+  uint8_t Mb[XR6::N];                    // M_{k-1} on R6
+  uint32_t Mw[G::TH + 12][G::MWORDS];    // M_{k-1} words of the R6 rows (clamped rows)
+  float S[G::template Reg<2>::N];        // S on R2
+  float N[G::TH * G::TW];                // N on the tile
+  float M3[G::template Reg<3>::N];       // med3(I) on R3
+  uint16_t list[G::template Reg<4>::N];  // work lists: replacement on R4; then fine-structure
+                                         // items from the front and S'-only items from the back
+  uint8_t flags[G::TH * G::TW];          // bit3: saturated
+  uint32_t pw[3][G::TH][G::TWW];         // the tile's sig, lo and candidate bit-plane words
+  uint32_t Sw[G::TH][G::TWW];            // satgrow > 0: the tile's words of the grown saturated set
+  unsigned nlist, nlist2;                // list lengths (S'-only, fine-structure)
+  unsigned nfine;                        // F evaluations of the tile
 };
-template <> struct CoreSmemT<uint16_t> {
-  uint16_t X[XR6::N];            // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
+template <class G> struct CoreSmemT<G, uint16_t> {
+  using XR6 = typename G::XR6;
+  uint16_t X[XR6::N];                    // X0 on R6, then I_{k-1} on R4 (uint16 frames stay integral)
   uint8_t Mb[XR6::N];
-  uint32_t Mw[TH + 12][MWORDS];
-  float S[Reg<2>::N];
-  float2 DY[Reg<2>::N];          // {2N, 1/(2N)} on R2 (the table at med5(I))
-  uint16_t M3[Reg<3>::N];
-  uint16_t list[Reg<4>::N];
-  uint8_t flags[TH * TW];
-  uint32_t pw[3][TH][TWW];
-  uint32_t Sw[TH][TWW];
+  uint32_t Mw[G::TH + 12][G::MWORDS];
+  float S[G::template Reg<2>::N];
+  float2 DY[G::template Reg<2>::N];      // {2N, 1/(2N)} on R2 (the table at med5(I))
+  uint16_t M3[G::template Reg<3>::N];
+  uint16_t list[G::template Reg<4>::N];
+  uint8_t flags[G::TH * G::TW];
+  uint32_t pw[3][G::TH][G::TWW];
+  uint32_t Sw[G::TH][G::TWW];
   unsigned nlist, nlist2;
   unsigned nfine;
 };
-static_assert(TH * TW <= Reg<4>::N, "both sparse lists of a tile fit in one list array");
 // Alignment of the vector accesses: 16-byte staging rows (X; Mb in 8-byte
-// groups), 4-pixel block-network loads, 2-pixel pairs of S, N, DY and flags.
-template <class T>
+// groups), 4-pixel block-network loads, 2-pixel pairs of S, N, DY and flags;
+// both sparse lists of a tile fit in one list array, and list entries (tile
+// and region indices) fit in 16 bits.
+template <class G>
 constexpr bool core_layout_ok() {
-  return offsetof(T, X) % 16 == 0 && offsetof(T, Mb) % 8 == 0 && offsetof(T, S) % 8 == 0 &&
-         offsetof(T, flags) % 8 == 0;
+  using F = CoreSmemT<G, float>;
+  using U = CoreSmemT<G, uint16_t>;
+  return offsetof(F, X) % 16 == 0 && offsetof(F, Mb) % 8 == 0 && offsetof(F, S) % 8 == 0 &&
+         offsetof(F, flags) % 8 == 0 && offsetof(U, X) % 16 == 0 && offsetof(U, Mb) % 8 == 0 &&
+         offsetof(U, S) % 8 == 0 && offsetof(U, flags) % 8 == 0 && offsetof(F, N) % 8 == 0 &&
+         offsetof(U, DY) % 16 == 0 && G::TH * G::TW <= G::template Reg<4>::N && G::XR6::N <= 65536;
 }
-static_assert(core_layout_ok<CoreSmemT<float>>() && core_layout_ok<CoreSmemT<uint16_t>>(), "core layout");
-static_assert(offsetof(CoreSmemT<float>, N) % 8 == 0 && offsetof(CoreSmemT<uint16_t>, DY) % 16 == 0,
-              "core layout");
-// Dynamic shared memory of a core launch, by working-image type.
-template <class XT>
-constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<XT>);
+static_assert(core_layout_ok<G32x64>() && core_layout_ok<G64x64>() && core_layout_ok<G32x128>(), "core layout");
+// Dynamic shared memory of a core launch, by geometry and working-image type.
+template <class G, class XT>
+constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<G, XT>);
 
 __device__ __forceinline__ U16x2 pack2(uint16_t lo, uint16_t hi) {
   return U16x2{(uint32_t)lo | ((uint32_t)hi << 16)};
@@ -761,25 +786,25 @@ __device__ __forceinline__ float lplus_int(int vc, int up, int dn, int lf, int r
 // Block-network inputs from the staged image, 4 aligned pixels per shared
 // load (the network asks for each input once; loads of the same group are
 // merged).  Window column 0 must sit on a 4-pixel boundary of the row.
-template <int P>
+template <int P, int W>
 struct QuadLoaderF32 {
-  const float* base;  // window element (0, 0)
+  const float* base;  // window element (0, 0); rows W apart
   __device__ __forceinline__ float operator()(int i) const {
     const int a = i / P, b = i % P;
-    const float4 q = *reinterpret_cast<const float4*>(base + a * XR6::W + (b & ~3));
+    const float4 q = *reinterpret_cast<const float4*>(base + a * W + (b & ~3));
     return (b & 3) == 0 ? q.x : (b & 3) == 1 ? q.y : (b & 3) == 2 ? q.z : q.w;
   }
 };
 // Packed pairs for uint16 frames: low half from the window row, high half
 // from the row DY further down.
-template <int P, int DY>
+template <int P, int DY, int W>
 struct QuadLoaderU16 {
-  const uint16_t* base;
+  const uint16_t* base;  // rows W apart
   __device__ __forceinline__ U16x2 operator()(int i) const {
     const int a = i / P, b = i % P;
-    const uint16_t* p = base + a * XR6::W + (b & ~3);
+    const uint16_t* p = base + a * W + (b & ~3);
     const uint2 lo = *reinterpret_cast<const uint2*>(p);
-    const uint2 hi = *reinterpret_cast<const uint2*>(p + DY * XR6::W);
+    const uint2 hi = *reinterpret_cast<const uint2*>(p + DY * W);
     const uint32_t l = (b & 2) ? lo.y : lo.x, h = (b & 2) ? hi.y : hi.x;
     return U16x2{__byte_perm(l, h, (b & 1) ? 0x7632 : 0x5410)};
   }
@@ -789,7 +814,7 @@ struct QuadLoaderU16 {
 // units first, the med3 units after them starting at a warp boundary, so
 // that no warp runs both kinds (a warp with both would execute the two
 // networks one after the other).
-template <int S_UNITS, int M_UNITS>
+template <int NT, int S_UNITS, int M_UNITS>
 struct UnitMap {
   static constexpr int RS = (S_UNITS + NT - 1) / NT;     // rounds with med5 units
   static constexpr int REM = S_UNITS - (RS - 1) * NT;    // med5 units in the last of them
@@ -812,8 +837,10 @@ struct UnitMap {
 // four pixels per item, by the threads from FIRST on (for uint16 frames the
 // block threads without a med5 block, which would otherwise wait at the next
 // barrier).
-template <class XT, int FIRST, class SM>
+template <class G, class XT, int FIRST, class SM>
 __device__ __forceinline__ void sat_flags(const FrameDesc& f, SM& sm) {
+  constexpr int TH = G::TH, TW = G::TW, NT = G::NT;
+  using XR6 = typename G::XR6;
   static_assert(FIRST >= 0 && FIRST < NT, "some threads must take the flags");
   constexpr int first = FIRST;
   const int tid = (int)threadIdx.x;
@@ -855,11 +882,16 @@ __device__ __forceinline__ void sat_flags(const FrameDesc& f, SM& sm) {
 // Dense networks for float32 frames: med5 on R2 by 4x2 blocks (parked in
 // S), med3 on R3 by 8x2 blocks.  Blocks also evaluate out-of-frame
 // positions (from clamped inputs); those are overwritten by the edge fill.
-__device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& sm) {
+template <class G>
+__device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<G, float>& sm) {
+  constexpr int TH = G::TH, TW = G::TW, NT = G::NT;
+  using XR6 = typename G::XR6;
+  using R2 = typename G::template Reg<2>;
+  using R3 = typename G::template Reg<3>;
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_UY = (TH + 4) / S_BH;
   constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW, M_UY = (TH + 6) / M_BH;
   constexpr int S_UNITS = S_UX * S_UY;
-  using UM = UnitMap<S_UNITS, M_UX * M_UY>;
+  using UM = UnitMap<NT, S_UNITS, M_UX * M_UY>;
   static_assert((TW + 4) % S_BW == 0 && (TH + 4) % S_BH == 0 && (TH + 6) % M_BH == 0, "block tiling");
   // Window columns start at lx0 - 2 = 4u - 4 (med5) and lx0 - 1 = 8m - 4
   // (med3): 4-pixel aligned in the 8-column-halo staging rows; the med3
@@ -872,7 +904,7 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      const QuadLoaderF32<P> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
+      const QuadLoaderF32<P, XR6::W> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       float m5[S_BH * S_BW];
       if (f.sepmed)
         blk_sep5_4x2_ld<float>(ld, m5);
@@ -882,22 +914,22 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 #pragma unroll
       for (int r = 0; r < S_BH; ++r)
 #pragma unroll
-        for (int cc = 0; cc < S_BW; ++cc) sm.S[Reg<2>::idx(ly0 + r, lx0 + cc)] = m5[r * S_BW + cc];
+        for (int cc = 0; cc < S_BW; ++cc) sm.S[R2::idx(ly0 + r, lx0 + cc)] = m5[r * S_BW + cc];
     } else {
       const int m = u - S_UNITS;
       const int ly0 = -3 + (m / M_UX) * M_BH, lx0 = -3 + (m % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      const QuadLoaderF32<P> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
+      const QuadLoaderF32<P, XR6::W> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
       float m3[M_BH * M_BW];
       blk_med3_8x2_ld<float>(ld, m3);
 #pragma unroll
       for (int r = 0; r < M_BH; ++r)
 #pragma unroll
         for (int cc = 0; cc < M_BW; ++cc)
-          if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
+          if (lx0 + cc < TW + 3) sm.M3[R3::idx(ly0 + r, lx0 + cc)] = m3[r * M_BW + cc];
     }
   }
-  sat_flags<float, 0>(f, sm);  // units outnumber threads here: all threads share the flags
+  sat_flags<G, float, 0>(f, sm);  // units outnumber threads here: all threads share the flags
 }
 
 // Dense part for uint16 frames: the same blocks on packed uint16 pairs, two
@@ -905,13 +937,18 @@ __device__ __forceinline__ void dense_f32(const FrameDesc& f, CoreSmemT<float>& 
 // block the same distance further down -- so each min/max instruction
 // serves two outputs.  Each med5 indexes the N table right away (the
 // block's 16 loads are in flight together); {2N, 1/(2N)} goes to DY.
-__device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t>& sm) {
+template <class G>
+__device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<G, uint16_t>& sm) {
+  constexpr int TH = G::TH, TW = G::TW, NT = G::NT;
+  using XR6 = typename G::XR6;
+  using R2 = typename G::template Reg<2>;
+  using R3 = typename G::template Reg<3>;
   constexpr int S_BW = 4, S_BH = 2, S_UX = (TW + 4) / S_BW, S_PAIRS = (TH + 4) / S_BH / 2;
   constexpr int S_DY = S_PAIRS * S_BH;  // row offset of the second block of a pair
   constexpr int M_BW = 8, M_BH = 2, M_UX = (TW + 6 + M_BW - 1) / M_BW;
   constexpr int M_PAIRS = ((TH + 6) / M_BH + 1) / 2, M_DY = M_PAIRS * M_BH;
   constexpr int S_UNITS = S_UX * S_PAIRS;
-  using UM = UnitMap<S_UNITS, M_UX * M_PAIRS>;
+  using UM = UnitMap<NT, S_UNITS, M_UX * M_PAIRS>;
   static_assert(((TH + 4) / S_BH) % 2 == 0, "S row-pairs pair up");
   static_assert(UM::ROUNDS == 1, "one unit per thread");
   for (int rd = 0; rd < UM::ROUNDS; ++rd) {
@@ -920,7 +957,7 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
     if (u < S_UNITS) {
       const int ly0 = -2 + (u / S_UX) * S_BH, lx0 = -2 + (u % S_UX) * S_BW;
       constexpr int P = S_BW + 4;
-      const QuadLoaderU16<P, S_DY> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
+      const QuadLoaderU16<P, S_DY, XR6::W> ld{sm.X + XR6::idx(ly0 - 2, lx0 - 2)};
       U16x2 m5[S_BH * S_BW];
       if (f.sepmed)
         blk_sep5_4x2_ld<U16x2>(ld, m5);
@@ -932,12 +969,12 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
         for (int r = 0; r < S_BH; ++r)
 #pragma unroll
           for (int cc = 0; cc < S_BW; ++cc)
-            sm.DY[Reg<2>::idx(ly0 + h * S_DY + r, lx0 + cc)] = __ldg(f.ntab + half_of(m5[r * S_BW + cc], h));
+            sm.DY[R2::idx(ly0 + h * S_DY + r, lx0 + cc)] = __ldg(f.ntab + half_of(m5[r * S_BW + cc], h));
     } else {
       const int mu = u - S_UNITS;
       const int ly0 = -3 + (mu / M_UX) * M_BH, lx0 = -3 + (mu % M_UX) * M_BW;
       constexpr int P = M_BW + 2;
-      const QuadLoaderU16<P, M_DY> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
+      const QuadLoaderU16<P, M_DY, XR6::W> ld{sm.X + XR6::idx(ly0 - 1, lx0 - 1)};
       U16x2 m3[M_BH * M_BW];
       blk_med3_8x2_ld<U16x2>(ld, m3);
 #pragma unroll
@@ -948,11 +985,11 @@ __device__ __forceinline__ void dense_u16(const FrameDesc& f, CoreSmemT<uint16_t
           if (ty >= TH + 3) continue;
 #pragma unroll
           for (int cc = 0; cc < M_BW; ++cc)
-            if (lx0 + cc < TW + 3) sm.M3[Reg<3>::idx(ty, lx0 + cc)] = (uint16_t)half_of(m3[r * M_BW + cc], h);
+            if (lx0 + cc < TW + 3) sm.M3[R3::idx(ty, lx0 + cc)] = (uint16_t)half_of(m3[r * M_BW + cc], h);
         }
     }
   }
-  sat_flags<uint16_t, UM::MF>(f, sm);  // the med3 warps
+  sat_flags<G, uint16_t, UM::MF>(f, sm);  // the med3 warps
 }
 
 // Appends val(it) for every set bit `it` of each lane's `hits` to a shared
@@ -987,21 +1024,25 @@ __device__ __forceinline__ void warp_emit(uint32_t hits, unsigned* cnt, uint16_t
 // where S > t: pixels with S > sigclip (unsaturated) are fine-structure
 // items (S', then F where S' > sigclip), the others with S above the lower
 // threshold are S'-only items; elsewhere every test fails.
-template <class XT>
-__device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& sm, int oy, int ox) {
+template <class G, class XT>
+__device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<G, XT>& sm, int oy, int ox) {
+  constexpr int TH = G::TH, TW = G::TW, NT = G::NT;
+  using XR6 = typename G::XR6;
+  using R2 = typename G::template Reg<2>;
+  using R4 = typename G::template Reg<4>;
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
   // Horizontal pixel pairs (even columns): 2-pixel aligned shared accesses.
-  constexpr int PW = Reg<2>::W / 2;       // pairs per R2 row
-  constexpr int NP = PW * Reg<2>::Hh;     // pairs on R2
+  constexpr int PW = R2::W / 2;           // pairs per R2 row
+  constexpr int NP = PW * R2::Hh;         // pairs on R2
   constexpr int IT = (NP + NT - 1) / NT;  // pairs per thread
-  static_assert(Reg<2>::W % 2 == 0 && XR6::W % 2 == 0 && TW % 2 == 0 && 2 * IT <= 32, "pairs");
+  static_assert(R2::W % 2 == 0 && XR6::W % 2 == 0 && TW % 2 == 0 && 2 * IT <= 32, "pairs");
   uint32_t hits = 0, hits_f = 0;  // bit 2*it+e: pixel e of pair it is an S'-only / fine item
 #pragma unroll 1
   for (int it = 0; it < IT; ++it) {
     const int q = it * NT + (int)threadIdx.x;
     if (q >= NP) break;
     const int ly = q / PW - 2, lx = (q % PW) * 2 - 2;
-    const int c = XR6::idx(ly, lx), i2 = Reg<2>::idx(ly, lx);
+    const int c = XR6::idx(ly, lx), i2 = R2::idx(ly, lx);
     float S0, S1;
     if constexpr (kU16) {
       const auto ld2 = [&](int o) { return *reinterpret_cast<const uint32_t*>(sm.X + o); };
@@ -1053,7 +1094,7 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<XT>& 
     return (uint16_t)((q / PW - 2) * TW + (q % PW) * 2 - 2 + (bit & 1));
   };
   warp_emit(hits_f, &sm.nlist2, sm.list, -1, tix);
-  warp_emit(hits, &sm.nlist, sm.list, Reg<4>::N - 1, tix);
+  warp_emit(hits, &sm.nlist, sm.list, R4::N - 1, tix);
 }
 
 // Work counters of a tile (valid in thread 0).  A block sums them over its
@@ -1071,8 +1112,13 @@ __device__ __forceinline__ void flush_counts(FrameState* st, const TileCounts& c
   if (c.replace) atomicAdd(&st->n_replace, c.replace);
 }
 
-template <class XT>
-__device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT>& sm) {
+template <class G, class XT>
+__device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<G, XT>& sm) {
+  constexpr int TH = G::TH, TW = G::TW, TWW = G::TWW, NT = G::NT, MWORDS = G::MWORDS;
+  using XR6 = typename G::XR6;
+  using R2 = typename G::template Reg<2>;
+  using R3 = typename G::template Reg<3>;
+  using R4 = typename G::template Reg<4>;
   using KT = KeyOf<XT>;
   using K = typename KT::K;
   constexpr bool kU16 = std::is_same<XT, uint16_t>::value;
@@ -1098,7 +1144,7 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
 
   // Stage X0 and M_{k-1} on R6 at clamped coordinates.
   bool bad = false;
-  stage_x0_mask<6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
+  stage_x0_mask<G, 6>(f, Mp, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
   if (sat_words) sm.Sw[tid / TWW][tid % TWW] = sw;
   if (tid == 0) sm.nlist = 0;
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
@@ -1149,8 +1195,8 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     }
     __syncthreads();
     if (edge) {
-      for (int i = tid; i < Reg<4>::N; i += NT) {
-        const int ly = i / Reg<4>::W - 4, lx = i % Reg<4>::W - 4;
+      for (int i = tid; i < R4::N; i += NT) {
+        const int ly = i / R4::W - 4, lx = i % R4::W - 4;
         const int gy = oy + ly, gx = ox + lx;
         if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
         sm.X[XR6::idx(ly, lx)] = sm.X[XR6::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
@@ -1162,25 +1208,25 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
   // Dense part: med5 on R2 and med3 on R3 (register blocks of shared min/max
   // networks), then L+, N, S, the saturation flags and the S' list per pixel.
   if constexpr (kU16)
-    dense_u16(f, sm);
+    dense_u16<G>(f, sm);
   else
-    dense_f32(f, sm);
+    dense_f32<G>(f, sm);
   if (tid == 0) sm.nlist2 = 0;
   __syncthreads();
-  dense_pixels(f, sm, oy, ox);
+  dense_pixels<G, XT>(f, sm, oy, ox);
   __syncthreads();
   if (edge) {
-    for (int i = tid; i < Reg<2>::N; i += NT) {
-      const int ly = i / Reg<2>::W - 2, lx = i % Reg<2>::W - 2;
+    for (int i = tid; i < R2::N; i += NT) {
+      const int ly = i / R2::W - 2, lx = i % R2::W - 2;
       const int gy = oy + ly, gx = ox + lx;
       if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-      sm.S[i] = sm.S[Reg<2>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+      sm.S[i] = sm.S[R2::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
     }
-    for (int i = tid; i < Reg<3>::N; i += NT) {
-      const int ly = i / Reg<3>::W - 3, lx = i % Reg<3>::W - 3;
+    for (int i = tid; i < R3::N; i += NT) {
+      const int ly = i / R3::W - 3, lx = i % R3::W - 3;
       const int gy = oy + ly, gx = ox + lx;
       if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) continue;
-      sm.M3[i] = sm.M3[Reg<3>::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
+      sm.M3[i] = sm.M3[R3::idx(clampi(gy, 0, ny - 1) - oy, clampi(gx, 0, nx - 1) - ox)];
     }
   }
   // Steps 4-5 on the sparse items, one block-wide phase: S' = S - med5(S),
@@ -1195,11 +1241,11 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     const unsigned q = r * NT + ((r & 1) ? (NT - 1 - tid) : tid);
     if (q >= total) continue;
     const bool fine = q < n2;
-    const int i = fine ? sm.list[q] : sm.list[Reg<4>::N - 1 - (int)(q - n2)];
+    const int i = fine ? sm.list[q] : sm.list[R4::N - 1 - (int)(q - n2)];
     const int ly = i / TW, lx = i % TW;
-    const int c = Reg<2>::idx(ly, lx);
-    const float* wb = sm.S + c - 2 * Reg<2>::W - 2;
-    const auto ld5 = [&](int e) { return wb[(e / 5) * Reg<2>::W + e % 5]; };
+    const int c = R2::idx(ly, lx);
+    const float* wb = sm.S + c - 2 * R2::W - 2;
+    const auto ld5 = [&](int e) { return wb[(e / 5) * R2::W + e % 5]; };
     float m;
     if (f.sepmed)
       sep5x5_ld<float>(ld5, &m);
@@ -1211,9 +1257,9 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
     if (!sat && sp > f.lo) atomicOr(&sm.pw[1][ly][lx >> 5], bit);
     if (!fine || !(sp > f.sigclip)) continue;  // S'-only items have S' <= S <= sigclip
     atomicOr(&sm.pw[0][ly][lx >> 5], bit);
-    const int c3 = Reg<3>::idx(ly, lx);
-    const XT* w7 = sm.M3 + c3 - 3 * Reg<3>::W - 3;
-    const auto ld7 = [&](int e) { return KT::key(w7[(e / 7) * Reg<3>::W + e % 7]); };
+    const int c3 = R3::idx(ly, lx);
+    const XT* w7 = sm.M3 + c3 - 3 * R3::W - 3;
+    const auto ld7 = [&](int e) { return KT::key(w7[(e / 7) * R3::W + e % 7]); };
     K m7;
     med7x7_ld<K>(ld7, &m7);
     ++n_eval;
@@ -1248,15 +1294,16 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<XT
   return counts;
 }
 
-// MINB: resident CTAs per SM the register allocation is bounded for (the
-// variants trade registers, and so spills, against occupancy).  One kernel
+// G: the tile geometry (shape and threads); MINB: resident CTAs per SM the
+// register allocation is bounded for (the variants trade registers, and so
+// spills, against occupancy).  One kernel
 // per working-image type: a request orders its frames so that each type's
 // tiles form one contiguous item range [item_begin, item_end), and a launch
 // walks only its own range (its own queue head).
-template <int MINB, class XT>
-__global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                        unsigned item_begin, unsigned item_end, int k,
-                                                        unsigned* head) {
+template <class G, int MINB, class XT>
+__global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                           unsigned item_begin, unsigned item_end, int k,
+                                                           unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_item;
   __shared__ int s_run;
@@ -1291,7 +1338,8 @@ __global__ void __launch_bounds__(NT, MINB) core_kernel(const FrameDesc* __restr
     if (item >= item_end) break;
     if (!run) continue;
     const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    const TileCounts c = core_tile<XT>(f, k, (int)(item - f.tile_begin), *reinterpret_cast<CoreSmemT<XT>*>(smem_raw));
+    const TileCounts c = core_tile<G, XT>(f, k, (int)(item - f.tile_begin),
+                                         *reinterpret_cast<CoreSmemT<G, XT>*>(smem_raw));
     if (threadIdx.x == 0) {
       if (f.st != acc_st) {
         flush_counts(acc_st, acc);
@@ -1325,9 +1373,10 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 // `bits`, the new flags of word w of row y.
 __device__ __forceinline__ void mark_tiles(const FrameDesc& f, int kn, int y, int w, uint32_t bits) {
   const int x_lo = w * 32 + __ffs(bits) - 1, x_hi = w * 32 + 31 - __clz(bits);
-  const int tiles_y = (f.ny + TH - 1) / TH;
-  const int ty0 = max(0, floordiv(y - TH - 6, TH) + 1), ty1 = min(tiles_y - 1, (y + 6) / TH);
-  const int tx0 = max(0, floordiv(x_lo - TW - 6, TW) + 1), tx1 = min(f.tiles_x - 1, (x_hi + 6) / TW);
+  const int th = f.th, tw = f.tw;  // the core tiles of the request
+  const int tiles_y = (f.ny + th - 1) / th;
+  const int ty0 = max(0, floordiv(y - th - 6, th) + 1), ty1 = min(tiles_y - 1, (y + 6) / th);
+  const int tx0 = max(0, floordiv(x_lo - tw - 6, tw) + 1), tx1 = min(f.tiles_x - 1, (x_hi + 6) / tw);
   uint8_t* d = f.tflags + (size_t)(kn & 1) * tiles_of(f);
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) d[ty * f.tiles_x + tx] = 1;
@@ -1346,7 +1395,7 @@ __device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
 }
 
 constexpr int GB_H = 32, GB_W = 8;  // growth block: 32 rows x 8 words (one word per thread)
-static_assert(GB_H * GB_W == NT, "one word per thread");
+static_assert(GB_H * GB_W == kBlock, "one word per thread");
 
 __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, unsigned b) {
   int lo = 0, hi = nframes - 1;
@@ -1363,8 +1412,9 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
 // g2 = dil3(g1) & lo for its word, M_k = M_{k-1} | g2, and counts new flags.
 // Every global load of the block (candidate, sig, lo and mask words) is
 // issued up front, so the block waits for one memory round trip.
-__global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                  unsigned total_blocks, int k) {
+__global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                      unsigned total_blocks, int k) {
+  constexpr int NT = kBlock;
   constexpr int CW = GB_W + 4, CN = (GB_H + 4) * CW;  // candidate region
   constexpr int GW = GB_W + 2, GN = (GB_H + 2) * GW;  // g1 region
   constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
@@ -1435,13 +1485,25 @@ __global__ void __launch_bounds__(NT) grow_kernel(const FrameDesc* __restrict__ 
 
 template <class XT>
 struct FinalSmemT {
-  XT X[XR3::N];
-  uint8_t Mb[XR3::N];
-  uint32_t Mw[TH + 6][MWORDS];
-  uint16_t list[TH * TW];
+  XT X[FG::XR3::N];
+  uint8_t Mb[FG::XR3::N];
+  uint32_t Mw[FG::TH + 6][FG::MWORDS];
+  uint16_t list[FG::TH * FG::TW];
   unsigned nlist;
 };
 constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
+
+// The rare replacements whose 5x5 window is fully flagged: the 7x7 window
+// from shared memory, else wider windows from global memory.  Kept out of
+// line so that the common path's register allocation does not carry the
+// 49-key network.
+template <class XT>
+__device__ __noinline__ XT replace_wide(const FrameDesc& f, const uint32_t* M, const FinalSmemT<XT>& sm, int c,
+                                        int gy, int gx) {
+  XT v;
+  if (!maskmed7(sm.X, sm.Mb, FG::XR3::W, c, v)) v = (XT)maskmed_wide(f, M, gy, gx, 4);
+  return v;
+}
 
 // cleaned = R(X0, M_run) (the masked median at flagged pixels, X0 elsewhere),
 // mask = M_run as uint8, the flagged count and the iterations run.  The
@@ -1450,12 +1512,15 @@ constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
 // thread where the row pitch allows 16-byte stores.
 template <class XT>
 __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
+  constexpr int TH = FG::TH, TW = FG::TW, TWW = FG::TWW, NT = kBlock;
+  using XR3 = FG::XR3;
+  static_assert(FG::NT == kBlock, "finalize geometry");
   const int tid = threadIdx.x;
-  const int oy = (tix / f.tiles_x) * TH, ox = (tix % f.tiles_x) * TW;
+  const int oy = (tix / f.ftiles_x) * TH, ox = (tix % f.ftiles_x) * TW;
   const int run = run_of(f);
   const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
   bool bad = false;
-  stage_x0_mask<3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
+  stage_x0_mask<FG, 3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
   if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
   // The tile's flagged pixels straight from the staged mask words (the
@@ -1476,8 +1541,7 @@ __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& s
     const int ly = i / TW, lx = i % TW;
     const int c = XR3::idx(ly, lx);
     XT v;
-    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v) && !maskmed7(sm.X, sm.Mb, XR3::W, c, v))
-      v = (XT)maskmed_wide(f, M, oy + ly, ox + lx, 4);
+    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v)) v = replace_wide(f, M, sm, c, oy + ly, ox + lx);
     sm.X[c] = v;
   }
   __syncthreads();
@@ -1509,7 +1573,7 @@ __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& s
   return n;
 }
 
-__global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
+__global__ void __launch_bounds__(kBlock, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                          unsigned total, unsigned* head) {
   __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
   __shared__ unsigned s_item;
@@ -1525,8 +1589,8 @@ __global__ void __launch_bounds__(NT, 6) finalize_kernel(const FrameDesc* __rest
     __syncthreads();
     const unsigned item = s_item;
     if (item >= total) break;
-    const FrameDesc& f = fr[frame_of(fr, nframes, item)];
-    const int tix = (int)(item - f.tile_begin);
+    const FrameDesc& f = fr[frame_of_fin(fr, nframes, item)];
+    const int tix = (int)(item - f.fin_begin);
     unsigned n;
     if (f.dtype == 1) {
       auto& sm = *reinterpret_cast<FinalSmemT<uint16_t>*>(smem);

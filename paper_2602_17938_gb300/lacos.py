@@ -20,6 +20,7 @@ LACOS_F32, LACOS_U16 = 0, 1
 OK, PENDING = 0, 1
 EINVAL, EAGAIN, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNKNOWN_TICKET, ENOGAIN = -1, -2, -3, -4, -5, -6, -7, -8
 MAX_NITER = 256
+CORE_VARIANTS = 8  # LACOS_CORE_VARIANTS: core-kernel tile shape x occupancy variants
 _ERRNAMES = {EINVAL: "EINVAL", EAGAIN: "EAGAIN", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
              ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT", EUNKNOWN_TICKET: "EUNKNOWN_TICKET",
              ENOGAIN: "ENOGAIN"}
@@ -81,6 +82,8 @@ def load_library():
         lib.lacos_destroy.argtypes = [P]
         lib.lacos_scratch_bytes.argtypes = [I, I]
         lib.lacos_scratch_bytes.restype = ctypes.c_size_t
+        lib.lacos_request_bytes.argtypes = [I, I, ctypes.POINTER(Params)]
+        lib.lacos_request_bytes.restype = ctypes.c_size_t
         lib.lacos_last_cuda_error.argtypes = [P]
         lib.lacos_version.restype = ctypes.c_char_p
         lib.lacos_set_profiling.argtypes = [P, I]
@@ -201,7 +204,7 @@ class Context:
         Returns (best variant, [mean ms per variant])."""
         ny, nx = frame.shape
         best = ctypes.c_int(-1)
-        ms = (ctypes.c_float * 4)()
+        ms = (ctypes.c_float * CORE_VARIANTS)()
         rc = self.lib.lacos_autotune(self.h, ctypes.c_void_p(frame.data_ptr()), _dtype_code(frame), ny, nx,
                                      ctypes.byref(params), ctypes.c_void_p(mask.data_ptr()),
                                      ctypes.c_void_p(clean.data_ptr()), _stream_ptr(stream), int(reps),

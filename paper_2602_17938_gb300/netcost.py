@@ -43,6 +43,27 @@ def detect_minmax_ops(profile: dict) -> int:
                + profile["n_sprime"] * c["med5x5"])
 
 
+def detect_work(profile: dict, packed: bool) -> dict:
+    """Algorithmic min/max work of the core launches of one request, split by
+    kind and counted in instructions as well as element operations.
+
+    * dense: the shared-block med5 (noise model) and med3 networks at every
+      tile pixel the core kernel computed; on uint16 frames one packed
+      min/max.u16x2 instruction serves two outputs (``packed``);
+    * sprime: the standalone med5 of S at each S' evaluation (float keys);
+    * fine: the med7 of med3 at each fine-structure evaluation (one lane).
+    The masked-median replacement is not counted (its per-tile list includes
+    the halo that neighbouring tiles recompute)."""
+    c = counts()
+    px = profile.get("px_core", profile["px_iterations"])
+    dense = px * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
+    sprime = profile["n_sprime"] * c["med5x5"]
+    fine = profile["n_fine"] * c["med7x7"]
+    return {"dense_elem": dense, "dense_instr": dense / 2 if packed else dense,
+            "sprime_instr": sprime, "fine_instr": fine,
+            "instr": (dense / 2 if packed else dense) + sprime + fine}
+
+
 def fine_minmax_ops(profile: dict) -> int:
     return int(profile["n_fine"] * counts()["fine_per_px"])
 

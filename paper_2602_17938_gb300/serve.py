@@ -73,9 +73,12 @@ class Server:
         self._free = collections.defaultdict(list)  # (ny, nx) -> [(mask, clean)]
         self.in_use = 0
 
-    def _request_bytes(self, ny, nx):
-        lib = self.ctx.lib
-        return ny * nx * 5 + lib.lacos_scratch_bytes(ny, nx)
+    def _request_bytes(self, ny, nx, params):
+        """Device bytes of one request in flight: its outputs (uint8 mask and
+        float32 cleaned frame, 5 B/px) and the library scratch its parameters
+        need (one more bit-plane with satgrow > 0)."""
+        import ctypes
+        return ny * nx * 5 + self.ctx.lib.lacos_request_bytes(ny, nx, ctypes.byref(params))
 
     def _buffers(self, ny, nx):
         import torch
@@ -105,7 +108,7 @@ class Server:
                 i = queue[0]
                 rq = requests[i]
                 ny, nx = rq.frame.shape
-                need = self._request_bytes(ny, nx)
+                need = self._request_bytes(ny, nx, rq.params)
                 if self.in_use + need > self.budget and inflight:
                     break
                 mask, clean = self._buffers(ny, nx)

@@ -46,6 +46,36 @@ def test_host_only_entry_points(lib):
     assert lib.lacos_scratch_bytes(0, 5) == 0
 
 
+def test_request_bytes_counts_the_saturation_plane(lib):
+    from paper_2602_17938_gb300 import lacos
+    lib.lacos_scratch_bytes.restype = ctypes.c_size_t
+    lib.lacos_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.lacos_request_bytes.restype = ctypes.c_size_t
+    lib.lacos_request_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    base = lib.lacos_scratch_bytes(6388, 9576)
+    assert lib.lacos_request_bytes(6388, 9576, None) == base
+    p = lacos.make_params(1.0, 1.5)
+    assert lib.lacos_request_bytes(6388, 9576, ctypes.byref(p)) == base
+    p = lacos.make_params(1.0, 1.5, satgrow=2)
+    # one more bit-plane (6388 rows of 300 words), 256-byte aligned
+    plane = (6388 * 300 * 4 + 255) // 256 * 256
+    assert lib.lacos_request_bytes(6388, 9576, ctypes.byref(p)) == base + plane
+    assert lib.lacos_request_bytes(0, 9576, ctypes.byref(p)) == 0
+
+
+def test_batch_frame_count_limits_without_gpu(lib):
+    # The per-frame kernels put frames on the grid's y dimension: 1 <= n <= 65535.
+    # The count is checked before any pointer is read, so no context is needed.
+    f = lib.lacos_submit_batch
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8 + [ctypes.c_int, ctypes.c_void_p,
+                                                                             ctypes.c_void_p]
+    dummy = ctypes.c_void_p(16)
+    args = [dummy] * 8
+    for n in (0, -1, 65536, 1 << 30):
+        assert f(None, n, *args, 0, None, dummy) == -1, n
+
+
 def test_null_arguments_rejected_without_gpu(lib):
     lib.lacos_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
     assert lib.lacos_create(None, 0, 0, 0) == -1

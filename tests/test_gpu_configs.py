@@ -10,15 +10,20 @@
 
 * The largest frame the ABI accepts (46340 x 46340 uint16, 2.1e9 pixels).
 
-Outputs are compared bit for bit with the float32 oracle on sampled boxes
-(the oracle runs a crop with a 64-pixel margin, more than six iterations
-can reach), and every frame satisfies the any-size properties: cleaned
-equals input outside the mask and the flagged count equals the mask's sum.
+Every pixel of every frame of the batch and of the stress subset is compared
+bit for bit with the float32 oracle's whole-frame result (stored SHA-256
+digests of its mask and cleaned frame, written by
+tests/golden/make_full_frame_digests.py from the oracle alone).  Sampled
+boxes are also compared with live oracle runs on crops (a crop with a
+64-pixel margin, more than six iterations can reach), and every frame
+satisfies the any-size properties: cleaned equals input outside the mask
+and the flagged count equals the mask's sum.
 """
 import numpy as np
 import pytest
 
 import oracle
+from conftest import full_frame_digest_check
 from paper_2602_17938_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -97,6 +102,7 @@ def test_batch_of_64_mixed_frames(lacos):
     for i, (f, sp) in enumerate(zip(frames, specs)):
         m, c = masks[i].cpu().numpy(), cleans[i].cpu().numpy()
         _invariants(f, m, c, results[i])
+        full_frame_digest_check(2, i, f, m, c, results[i][1], results[i][2])
         if i in (0, 15, 16, 31, 32, 63):
             _check(f, sp, m, c, _boxes(f, rng))
 
@@ -111,6 +117,7 @@ def test_stress_subset_one_batched_launch(lacos):
     for i, (f, sp) in enumerate(zip(frames, specs)):
         m, c = masks[i].cpu().numpy(), cleans[i].cpu().numpy()
         _invariants(f, m, c, results[i])
+        full_frame_digest_check(4, 8 * i, f, m, c, results[i][1], results[i][2])
         assert results[i][1] <= sp.niter
         assert not m[f == 65535].any()  # saturated pixels are never flagged
         if sp.niter not in checked:

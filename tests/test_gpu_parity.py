@@ -1,10 +1,11 @@
 """GPU (CUDA path, through the C ABI) vs the float32 CPU oracle: bit-exact.
 
 The masks are compared byte for byte and the cleaned frames bit for bit;
-iters_run and n_flagged must match too.  Full-size frames are checked on
-sampled crops the oracle can finish in seconds (a crop with a 64-pixel
-margin reproduces the frame's result in its interior: one iteration reads
-at most 8 pixels away), plus properties that hold at any size.
+iters_run and n_flagged must match too.  The 61-Mpx frame is compared on
+every pixel with the oracle's whole-frame result (stored digests), and on
+sampled crops against live oracle runs (a crop with a 64-pixel margin
+reproduces the frame's result in its interior: one iteration reads at most
+8 pixels away), plus properties that hold at any size.
 """
 import math
 
@@ -304,10 +305,79 @@ def _sample_boxes(ny, nx, rng, n=10, size=48):
     return boxes
 
 
-def test_full_size_61mpx_uint16_sampled(ctx):
+def test_full_size_61mpx_uint16_every_pixel(ctx):
+    # Every pixel against the oracle's whole-frame run (stored digests), and
+    # sampled boxes against live oracle runs on crops with a 64-pixel margin.
+    from conftest import full_frame_digest_check
     spec = synth.config_specs(1)[0]
     f = synth.make_frame(spec)
     m, c, res = gpu_run(ctx, f, spec.gain, spec.readnoise, niter=spec.niter)
     assert res.status == 0 and res.n_flagged == int(m.sum()) > 0
+    full_frame_digest_check(1, 0, f, m, c, res.iters_run, res.n_flagged)
     np.testing.assert_array_equal(c[m == 0], f[m == 0].astype(np.float32))
     _crop_check(f, spec, m, c, _sample_boxes(*f.shape, np.random.default_rng(1)))
+
+
+def _variant_cases():
+    """Frames that cross tile borders of every core-kernel tile shape (32 x 64,
+    64 x 64, 32 x 128) with ragged edges, in both dtypes and the optional modes."""
+    cases = [(noisy_with_hits(300, 517, seed=71), 1.0, 1.5, {}),
+             (noisy_with_hits(97, 130, seed=72, dtype=np.uint16), 1.0, 1.5, {}),
+             (noisy_with_hits(70, 61, seed=73), 1.0, 1.5, dict(sepmed=True))]
+    spec = synth.FrameSpec(257, 389, "u16", (74, 0), sky=300.0, gain=0.8, readnoise=1.2, n_stars=12,
+                           n_tracks=400, hot_frac=0.005, salt_pepper=True)
+    sat = synth.make_frame(spec)
+    sat[100:104, 127:131] = 65535  # a saturated core across a 128-column tile border
+    cases.append((sat, spec.gain, spec.readnoise, dict(satgrow=2)))
+    rng = np.random.default_rng(75)
+    dense = (100 + 10 * rng.standard_normal((140, 200))).astype(np.float32)
+    dense[58:72, 120:136] += rng.uniform(0, 20000, (14, 16)).astype(np.float32)  # widened windows at a border
+    cases.append((dense, 1.0, 1.5, {}))
+    return cases
+
+
+def test_every_core_variant_bit_exact(ctx):
+    # Every tile shape x occupancy variant the autotuner can pick gives the
+    # oracle's result bit for bit.
+    from paper_2602_17938_gb300 import lacos
+    cases = _variant_cases()
+    refs = [oracle.run(f, g, rn, **{"satgrow": kw.get("satgrow", 0), "sepmed": kw.get("sepmed", False)})
+            for f, g, rn, kw in cases]
+    v0 = ctx.core_variant()
+    try:
+        for v in range(lacos.CORE_VARIANTS):
+            ctx.set_core_variant(v)
+            for (f, g, rn, kw), (m_ref, c_ref, it_ref, nf_ref) in zip(cases, refs):
+                m, c, res = gpu_run(ctx, f, g, rn, **kw)
+                assert np.array_equal(m, m_ref), (v, f.shape, int((m != m_ref).sum()))
+                assert np.array_equal(c.view(np.uint32), c_ref.view(np.uint32)), (v, f.shape)
+                assert (res.status, res.iters_run, res.n_flagged) == (0, it_ref, nf_ref), (v, f.shape)
+    finally:
+        ctx.set_core_variant(v0)
+
+
+def test_core_variants_on_the_batched_path(ctx):
+    # A mixed batch (both dtypes) through each tile shape: the per-frame tile
+    # ranges of the core and finalize queues differ when the core tile is not
+    # 32 x 64.
+    from paper_2602_17938_gb300 import lacos
+    cases = _variant_cases()[:4]
+    refs = [oracle.run(f, g, rn, **{"satgrow": kw.get("satgrow", 0), "sepmed": kw.get("sepmed", False)})
+            for f, g, rn, kw in cases]
+    d = [lacos.to_device(f) for f, _, _, _ in cases]
+    ps = [lacos.make_params(g, rn, **kw) for _, g, rn, kw in cases]
+    v0 = ctx.core_variant()
+    try:
+        for v in (3, 5, 7):
+            ctx.set_core_variant(v)
+            masks = [torch.empty(f.shape, dtype=torch.uint8, device="cuda") for f in d]
+            cleans = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in d]
+            t, per = ctx.submit_batch(d, ps, masks, cleans)
+            ctx.wait(t)
+            torch.cuda.synchronize()
+            for i, (m_ref, c_ref, it_ref, nf_ref) in enumerate(refs):
+                assert np.array_equal(masks[i].cpu().numpy(), m_ref), (v, i)
+                assert np.array_equal(cleans[i].cpu().numpy().view(np.uint32), c_ref.view(np.uint32)), (v, i)
+                assert (per[i].iters_run, per[i].n_flagged) == (it_ref, nf_ref), (v, i)
+    finally:
+        ctx.set_core_variant(v0)

@@ -82,7 +82,7 @@ def test_budget_limits_requests_in_flight(lib):
     f = lacos.to_device(_frame(512, 512, 5))
     p = lacos.make_params(1.0, 1.5)
     with serve.Server(0, hbm_budget_bytes=1, max_slots=8) as srv:
-        one = srv._request_bytes(512, 512)
+        one = srv._request_bytes(512, 512, p)
     # room for one request at a time (plus the context's scratch for it)
     with serve.Server(0, hbm_budget_bytes=int(1.5 * one), max_slots=8) as srv:
         st = srv.run([serve.Request(f, p, 0.0) for _ in range(5)])
@@ -114,7 +114,7 @@ def test_every_core_variant_bit_exact_and_autotune(lib, dtype, tmp_path, monkeyp
     m = torch.empty(f.shape, dtype=torch.uint8, device="cuda")
     c = torch.empty(f.shape, dtype=torch.float32, device="cuda")
     with lacos.Context(0) as ctx:
-        for v in range(4):
+        for v in range(lacos.CORE_VARIANTS):
             ctx.set_core_variant(v)
             assert ctx.core_variant() == v
             r = ctx.wait(ctx.submit(d, p, m, c))
@@ -124,7 +124,7 @@ def test_every_core_variant_bit_exact_and_autotune(lib, dtype, tmp_path, monkeyp
         monkeypatch.setenv("LACOS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
         from paper_2602_17938_gb300 import autotune
         best, ms = autotune.tune(ctx, d, p, m, c, reps=1)
-        assert 0 <= best <= 3 and ctx.core_variant() == best and len(ms) == 4
+        assert 0 <= best < lacos.CORE_VARIANTS and ctx.core_variant() == best and len(ms) == lacos.CORE_VARIANTS
         best2, ms2 = autotune.tune(ctx, d, p, m, c)  # from the cache
         assert best2 == best and ms2 is None
 

@@ -137,12 +137,16 @@ def test_recovers_the_gain_of_synthetic_poisson_frames(g, rn, mu):
 def test_flagged_or_saturated_partner_removes_the_pair():
     rng = np.random.default_rng(7)
     I = np.rint(rng.normal(500.0, 25.0, (64, 96))).astype(np.float32)
-    kept_cols = [c for c in range(96) if c not in (4, 5, 30, 31)]
-    ref = oracle.estimate_gain(I[:, kept_cols], np.zeros((64, 92), np.uint8), np.zeros((64, 92), np.uint8), 4.0)
+    gone = (4, 5, 30, 31, 60, 61, 70, 71)
+    kept_cols = [c for c in range(96) if c not in gone]
+    z = np.zeros((64, 96 - len(gone)), np.uint8)
+    ref = oracle.estimate_gain(I[:, kept_cols], z, z, 4.0)
     M = np.zeros(I.shape, np.uint8)
     sat = np.zeros(I.shape, np.uint8)
-    M[:, 4] = 1     # one pixel of pair (4, 5) flagged
-    sat[:, 31] = 1  # one pixel of pair (30, 31) saturated
+    M[:, 4] = 1     # the first pixel of pair (4, 5) flagged
+    M[:, 61] = 1    # the second pixel of pair (60, 61) flagged
+    sat[:, 31] = 1  # the second pixel of pair (30, 31) saturated
+    sat[:, 70] = 1  # the first pixel of pair (70, 71) saturated
     assert oracle.estimate_gain(I, M, sat, 4.0) == ref
 
 

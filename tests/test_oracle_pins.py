@@ -603,3 +603,42 @@ def test_golden_threshold_strictness():
                                 gd["sigfrac"], gd["objlim"])
     assert d["Sp"][qy, qx] == np.float32(case["Sp_q"])
     assert sorted(map(list, zip(*np.nonzero(M)))) == case["mask"]
+
+
+def test_golden_lower_threshold_strictness():
+    # growth.json, fifth case: S'(q) equals sigfrac*sigclip exactly in float32;
+    # q is grown only by a non-strict test.
+    gd = _load_golden("growth.json")
+    case = gd["cases"][4]
+    ny, nx = gd["shape"]
+    (py, px), (qy, qx) = gd["p"], gd["q"]
+    x0 = np.full((ny, nx), gd["sky"], np.float32)
+    x0[py, px] += gd["amp_p"]
+    x0[qy, qx] += case["b"]
+    sat = np.zeros((ny, nx), np.uint8)
+    _, _, M, d = oracle.iterate(x0, sat, x0, sat, gd["gain"], gd["readnoise"], gd["sigclip"],
+                                gd["sigfrac"], gd["objlim"])
+    lo = np.float32(gd["sigfrac"]) * np.float32(gd["sigclip"])
+    assert d["Sp"][qy, qx] == lo == np.float32(case["Sp_q"])
+    assert sorted(map(list, zip(*np.nonzero(M)))) == case["mask"]
+
+
+def test_saturated_pixel_seeds_no_growth():
+    # Reading C9: a saturated pixel is never a candidate, so nothing grows from
+    # it.  A sharp saturated pixel sits on the wing of a resolved star (FWHM 3,
+    # peak 10000 ADU), two pixels from its centre.  Five of its neighbours have
+    # S' > sigclip but fail the objlim test (the star is resolved: med3 - med7
+    # is large there), so nothing is a candidate and nothing is flagged; a
+    # saturated candidate would grow into those neighbours.
+    yy, xx = np.mgrid[0:32, 0:32]
+    s = 3.0 / 2.3548
+    f = (100.0 + 10000.0 * np.exp(-((yy - 16) ** 2 + (xx - 16) ** 2) / (2 * s * s))).astype(np.float32)
+    f[16, 18] = 65535.0
+    sat = (f >= 60000.0).astype(np.uint8)
+    _, _, M, d = oracle.iterate(f, sat, f, np.zeros(f.shape, np.uint8), 1.0, 1.5, 4.5, 0.3, 5.0)
+    nb = [(16 + a, 18 + b) for a in (-1, 0, 1) for b in (-1, 0, 1) if (a, b) != (0, 0)]
+    assert sum(d["Sp"][q] > 4.5 and d["Sp"][q] / d["F"][q] <= 5.0 for q in nb) >= 3  # fail objlim only
+    assert d["Sp"][16, 18] > 4.5 and d["Sp"][16, 18] / d["F"][16, 18] > 5.0  # sharp: passes both tests
+    assert d["cand"].sum() == 0 and M.sum() == 0
+    m, _, _, nf = oracle.run(f, 1.0, 1.5, satlevel=60000.0, niter=4)
+    assert nf == 0 and m.sum() == 0

@@ -15,6 +15,8 @@ import math
 import numpy as np
 import pytest
 
+import oracle
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -55,6 +57,17 @@ def test_static_entry_point_matches_submit_twice():
             assert r.iters_run == r_ref.iters_run and r.n_flagged == r_ref.n_flagged > 0
             assert torch.equal(m, m_ref)
             assert torch.equal(c.view(torch.int32), c_ref.view(torch.int32))
+            assert r.latency_ms > 0.0  # host time of the blocking call
+        # The first case also straight against the float32 CPU oracle.
+        frame, gain, niter, _ = cases[0]
+        d = lacos.to_device(frame)
+        m = torch.empty(frame.shape, dtype=torch.uint8, device="cuda")
+        c = torch.empty(frame.shape, dtype=torch.float32, device="cuda")
+        r = lacos.run_static(d, lacos.make_params(gain, 1.5, niter=niter), m, c)
+        m_o, c_o, it_o, nf_o = oracle.run(frame, gain, 1.5, niter=niter)
+        assert r.status == 0 and r.iters_run == it_o and r.n_flagged == nf_o
+        assert np.array_equal(m.cpu().numpy(), m_o)
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), c_o.view(np.uint32))
 
 
 def test_static_entry_point_rejects_oversize_frames():
@@ -69,4 +82,38 @@ def test_static_entry_point_rejects_oversize_frames():
     c = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
     with pytest.raises(lacos.LacosError) as e:
         lacos.run_static(d, lacos.make_params(1.0, 1.5), m, c)
+    assert e.value.code == lacos.ENOMEM
+
+
+def test_static_limit_depends_on_the_saturation_plane():
+    # A frame just inside the array with five bit-planes runs; with saturated-star
+    # protection (a sixth plane) the same frame no longer fits and is rejected.
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    from paper_2602_17938_gb300 import build, lacos
+    build.build()
+    lib = lacos.load_library()
+    ny, nx = 10000, 9576
+    p0, p1 = lacos.make_params(1.0, 1.5, niter=2), lacos.make_params(1.0, 1.5, niter=2, satgrow=1)
+    assert lib.lacos_request_bytes(ny, nx, ctypes.byref(p0)) <= lacos.STATIC_SCRATCH_BYTES
+    assert lib.lacos_request_bytes(ny, nx, ctypes.byref(p1)) > lacos.STATIC_SCRATCH_BYTES
+    g = torch.Generator(device="cuda").manual_seed(10000)
+    f = torch.randn((ny, nx), generator=g, device="cuda").mul_(11.0).add_(120.0)
+    idx = torch.randint(0, ny * nx, (ny * nx // 200,), generator=g, device="cuda")
+    f.view(-1).index_add_(0, idx, torch.rand(idx.numel(), generator=g, device="cuda").mul_(3000.0).add_(200.0))
+    d = f.round_().clamp_(0, 65535).to(torch.int32).to(torch.int16).view(torch.uint16)
+    del f, idx
+    m = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    c = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+    r = lacos.run_static(d, p0, m, c)
+    m_ref = torch.empty_like(m)
+    c_ref = torch.empty_like(c)
+    with lacos.Context(0) as ctx:
+        r_ref = ctx.wait(ctx.submit(d, p0, m_ref, c_ref))
+    torch.cuda.synchronize()
+    assert r.status == 0 and r.n_flagged == r_ref.n_flagged > 0 and r.iters_run == r_ref.iters_run
+    assert torch.equal(m, m_ref) and torch.equal(c.view(torch.int32), c_ref.view(torch.int32))
+    with pytest.raises(lacos.LacosError) as e:
+        lacos.run_static(d, p1, m, c)
     assert e.value.code == lacos.ENOMEM
