@@ -611,7 +611,7 @@ def run_ours(args):
 def run_profile_case():
     """The case the per-kernel ncu summaries are taken on: a 9576 x 8000 uint16
     frame of the 61-Mpx recipe (153 MB, more than L2), cleaned twice through the
-    C ABI -- default parameters (ntab, core, grow, finalize kernels), then with
+    C ABI -- default parameters (ntab, core, grow, emit, replace kernels), then with
     the gain estimated and saturated-star protection (satseed, satgrow,
     gain_pass, ntab_level kernels) -- at niter=4."""
     import torch

@@ -27,8 +27,9 @@
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
  * its scratch (5 bits per pixel, 6 with satgrow > 0, plus 512 KiB and 3
- * bytes per 32x64 tile per frame; lacos_request_bytes gives the figure),
- * charged against the context's HBM budget.
+ * bytes per 32x64 tile per frame, and 1.5 MiB for a frame whose gain is
+ * estimated; lacos_request_bytes gives the figure), charged against the
+ * context's HBM budget.
  *
  * Errors: every call returns an int status; 0 is success.  Negative values
  * are the LACOS_E* codes below; lacos_poll also returns LACOS_PENDING (1).
@@ -209,7 +210,8 @@ int lacos_last_profile(lacos_ctx *c, lacos_profile *out);
  * scratch (lacos_request_bytes(ny, nx, p)) exceeds it are rejected with
  * LACOS_ENOMEM: above about 106 Mpx with satgrow = 0 (five bit-planes;
  * 9576 x 6388 fits, 12000 x 12000 does not), above about 88 Mpx with
- * satgrow > 0 (a sixth plane holds the grown saturated set).  Arguments,
+ * satgrow > 0 (a sixth plane holds the grown saturated set); an estimated
+ * gain needs 1.5 MiB more for its histogram.  Arguments,
  * layout and results are those of lacos_submit (outputs written to the
  * caller's d_mask and d_clean), except res->latency_ms: the host time from
  * entry to return, since the call queues the work on `stream`, waits for it
@@ -251,8 +253,8 @@ int lacos_destroy(lacos_ctx *c);
 size_t lacos_scratch_bytes(int ny, int nx);
 
 /* Scratch bytes a request for one ny x nx frame with parameters *p (NULL:
- * defaults) is charged against the budget; satgrow > 0 adds one bit-plane.
- * 0 for empty extents. */
+ * defaults) is charged against the budget; satgrow > 0 adds one bit-plane,
+ * gain = 0 the 1.5 MiB histogram of the gain estimate.  0 for empty extents. */
 size_t lacos_request_bytes(int ny, int nx, const lacos_params *p);
 
 /* Last CUDA error code seen by the context (0 if none). */
