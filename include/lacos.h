@@ -184,7 +184,9 @@ int lacos_submit_batch(lacos_ctx *c, int n, const void *const *d_frames, const i
  * its stream, so requests replayed from a CUDA graph are not profiled). */
 typedef struct {
   int n_levels;                        /* iteration levels launched */
-  float core_ms[LACOS_MAX_NITER];      /* per level: step 7 of the previous level, steps 1-5 */
+  float core_ms[LACOS_MAX_NITER];      /* per level: step 7 of the previous level, steps 1-5; when
+                                          the gain is estimated, also that level's estimate (the
+                                          pair histogram, its clipping rounds and the N table) */
   float grow_ms[LACOS_MAX_NITER];      /* per level: step 6 (growth, mask update) */
   float final_ms;                      /* cleaned frame (last step 7) and uint8 mask */
   long long px_iterations;             /* sum over frames of ny*nx*iters_run */

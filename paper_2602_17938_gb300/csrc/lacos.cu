@@ -8,7 +8,7 @@
 // queued on the caller's stream:
 //   memcpy(descriptors) ; memset(state, heads, M_0) ; ntab_kernel ;
 //   { core_kernel<u16>(k) ; core_kernel<f32>(k) ; grow_kernel(k) } for k = 1..max niter ;
-//   emit_kernel ; replace_kernel ;
+//   finalize_kernel ;
 // (each core kernel only where the request has frames of its dtype).
 //   memcpy(state -> pinned host) ; event.
 // Polling queries the event, reads the pinned state and frees the slot.
@@ -16,7 +16,7 @@
 // upload before and the outputs' download after that sequence.  The kernel
 // sequences of host requests whose frame fills the GPU kChainWaves times
 // over are chained through one context event (each waits for the previous
-// such request's output passes), so that requests in flight run their
+// such request's finalize_kernel), so that requests in flight run their
 // kernels one after another while the copies of the requests before and
 // after overlap them, instead of sharing the SMs, finishing together and
 // then downloading back to back.  Smaller frames cannot fill the GPU alone
@@ -47,10 +47,10 @@ constexpr size_t kNtabBytes = 65536 * sizeof(float2);  // {2N, 1/(2N)} per uint1
 // count (u32) and a sum of a + b (u64) per d.
 constexpr size_t kGainHistN = ((size_t)kGainBins * sizeof(unsigned) + 255) / 256 * 256;
 constexpr size_t kGainHistBytes = kGainHistN + ((size_t)kGainBins * sizeof(unsigned long long) + 255) / 256 * 256;
-// Tile-queue heads: one per (core kernel dtype, level).
+// Tile-queue heads: one per (core kernel dtype, level) plus the final replace.
 constexpr int kHeadLevels = LACOS_MAX_NITER + 1;
 constexpr int kHeadCore = 0;  // + dtype * kHeadLevels + level
-constexpr int kHeads = 2 * kHeadLevels;
+constexpr int kHeadFinal = 2 * kHeadLevels, kHeads = kHeadFinal + 1;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 struct FrameReq {
@@ -168,6 +168,7 @@ struct lacos_ctx {
   int num_sms = 0;
   int core_variant = kDefaultCoreVariant;  // index into kCoreVariants
   int blocks_per_sm_core_v[2][LACOS_CORE_VARIANTS] = {};  // resident CTAs by dtype and variant
+  int blocks_per_sm_final = 1;
   bool profiling = false;
   lacos_profile last_prof{};
   cudaEvent_t host_chain = nullptr;     // end of the last host request's kernels
@@ -244,7 +245,7 @@ static void launch_gain_level(const FrameDesc* ddesc, int nf, int k, int num_sms
 
 // `chain`, when given, is waited on before the first kernel (after the
 // descriptor copy and memsets, which touch only this slot's scratch) and
-// recorded after the output passes (before the state copy, which may queue
+// recorded after finalize_kernel (before the state copy, which may queue
 // behind another request's download).
 static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, const Layout& L,
                    cudaStream_t s, bool prof, cudaEvent_t chain = nullptr) {
@@ -256,8 +257,8 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   FrameState* dstate = (FrameState*)(d + L.states);
   // Host descriptors in the pinned buffer (states come back after them).
   FrameDesc* hdesc = (FrameDesc*)sl.hpinned;
-  unsigned total = 0, total_rblk = 0;
-  unsigned long long total_words = 0, total_chunks = 0;
+  unsigned total = 0, total_fin = 0;
+  unsigned long long total_words = 0;
   unsigned total_gblk = 0;
   int max_niter = 0;
   // Descriptor order: uint16 frames first, so that each dtype's tiles form
@@ -321,15 +322,15 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
     total += tiles;
     h.tile_end = total;
     if (f.dtype == LACOS_U16) tiles_u16 = total;
-    h.chunk_begin = total_chunks;
-    total_chunks += (unsigned long long)f.ny * (unsigned long long)((f.nx + kEmitPx - 1) / kEmitPx);
-    h.rblk_begin = total_rblk;
-    total_rblk += (unsigned)(((unsigned long long)f.ny * h.wpr + kBlock - 1) / kBlock);
+    h.ftiles_x = (f.nx + FG::TW - 1) / FG::TW;
+    h.fin_begin = total_fin;
+    total_fin += (unsigned)h.ftiles_x * (unsigned)((f.ny + FG::TH - 1) / FG::TH);
+    h.fin_end = total_fin;
     h.word_begin = total_words;
     total_words += (unsigned long long)f.ny * h.wpr;
-    h.gblk_x = (unsigned)((h.wpr + kGrowOut - 1) / kGrowOut);
+    h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
     h.gblk_begin = total_gblk;
-    total_gblk += h.gblk_x * (unsigned)((f.ny + kGrowRows - 1) / kGrowRows);
+    total_gblk += h.gblk_x * (unsigned)((f.ny + GB_H - 1) / GB_H);
     max_niter = std::max(max_niter, f.p.niter);
   }
   CK(cudaMemcpyAsync(ddesc, hdesc, sizeof(FrameDesc) * fr.size(), cudaMemcpyHostToDevice, s));
@@ -349,10 +350,9 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
   for (int dt = 0; dt < 2; ++dt)
     gdt[dt] = std::min<unsigned>(rng[dt][1] - rng[dt][0],
                                  (unsigned)(c->num_sms * c->blocks_per_sm_core_v[dt][cv]));
-  const unsigned gem = (unsigned)std::min<unsigned long long>((total_chunks + kBlock - 1) / kBlock,
-                                                               (unsigned long long)c->num_sms * 32);
+  const unsigned gfi = std::min<unsigned>(total_fin, (unsigned)(c->num_sms * c->blocks_per_sm_final));
   // Profile events: [0] start, level k: [2k-1] after core, [2k] after grow,
-  // [2n+1] after the output passes (emit, replace).
+  // [2n+1] after finalize.
   const int nev = 2 * max_niter + 2;
   if (chain) CK(cudaStreamWaitEvent(s, chain, 0));
   if (prof) {
@@ -388,12 +388,11 @@ static int enqueue(lacos_ctx* c, Slot& sl, const std::vector<FrameReq>& fr, cons
       CK(cudaGetLastError());
     }
     if (int rc = mark(2 * k - 1)) return rc;
-    grow_kernel<<<(total_gblk + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(ddesc, nf, total_gblk, k);
+    grow_kernel<<<total_gblk, kBlock, 0, s>>>(ddesc, nf, total_gblk, k);
     CK(cudaGetLastError());
     if (int rc = mark(2 * k)) return rc;
   }
-  emit_kernel<<<gem, kBlock, 0, s>>>(ddesc, nf, total_chunks);
-  replace_kernel<<<total_rblk, kBlock, 0, s>>>(ddesc, nf, total_rblk);
+  finalize_kernel<<<gfi, kBlock, 0, s>>>(ddesc, nf, total_fin, heads + kHeadFinal);
   CK(cudaGetLastError());
   if (int rc = mark(2 * max_niter + 1)) return rc;
   if (chain) CK(cudaEventRecord(chain, s));
@@ -634,10 +633,13 @@ int lacos_create(lacos_ctx** out, int device, size_t hbm_budget_bytes, int max_s
     const int v = std::atoi(env);
     if (v >= 0 && v < LACOS_CORE_VARIANTS) c->core_variant = v;
   }
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm_final, finalize_kernel, kBlock, 0);
   if (e != cudaSuccess) {
     delete c;
     return LACOS_ECUDA;
   }
+  c->blocks_per_sm_final = std::max(1, c->blocks_per_sm_final);
   *out = c;
   return LACOS_OK;
 }
@@ -810,7 +812,7 @@ __device__ __align__(256) unsigned char g_static_scratch[LACOS_STATIC_SCRATCH_BY
 struct StaticDevice {
   bool ready = false;
   void* scratch = nullptr;  // device address of g_static_scratch on this device
-  int num_sms = 0, bpsm_core[2] = {1, 1}, core_variant = kDefaultCoreVariant;
+  int num_sms = 0, bpsm_core[2] = {1, 1}, bpsm_final = 1, core_variant = kDefaultCoreVariant;
 };
 std::mutex g_static_mu;
 constexpr int kStaticMaxDevices = 64;
@@ -839,7 +841,10 @@ cudaError_t static_setup(int dev, StaticDevice*& out) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_core[dt], V.fn[dt], V.nt, V.smem[dt]);
       sd.bpsm_core[dt] = std::max(1, sd.bpsm_core[dt]);
     }
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sd.bpsm_final, finalize_kernel, kBlock, 0);
     if (e != cudaSuccess) return e;
+    sd.bpsm_final = std::max(1, sd.bpsm_final);
     sd.ready = true;
   }
   out = &sd;
@@ -920,14 +925,14 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   const unsigned total = (unsigned)h.tiles_x * (unsigned)((ny + V.th - 1) / V.th);
   h.tile_begin = 0;
   h.tile_end = total;
-  h.chunk_begin = 0;
-  const unsigned long long total_chunks = (unsigned long long)ny * (unsigned long long)((nx + kEmitPx - 1) / kEmitPx);
-  h.rblk_begin = 0;
-  const unsigned total_rblk = (unsigned)(((unsigned long long)ny * h.wpr + kBlock - 1) / kBlock);
+  h.ftiles_x = (nx + FG::TW - 1) / FG::TW;
+  const unsigned total_fin = (unsigned)h.ftiles_x * (unsigned)((ny + FG::TH - 1) / FG::TH);
+  h.fin_begin = 0;
+  h.fin_end = total_fin;
   h.word_begin = 0;
-  h.gblk_x = (unsigned)((h.wpr + kGrowOut - 1) / kGrowOut);
+  h.gblk_x = (unsigned)((h.wpr + GB_W - 1) / GB_W);
   h.gblk_begin = 0;
-  const unsigned total_gblk = h.gblk_x * (unsigned)((ny + kGrowRows - 1) / kGrowRows);
+  const unsigned total_gblk = h.gblk_x * (unsigned)((ny + GB_H - 1) / GB_H);
 
   // The array keeps the previous call's contents: the descriptor is
   // rewritten, and the queue heads, the state and M_0 are cleared.
@@ -941,8 +946,7 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
     return LACOS_ECUDA;
   const int di = f.dtype == LACOS_U16 ? 1 : 0;
   const unsigned gd = std::min<unsigned>(total, (unsigned)(sd->num_sms * sd->bpsm_core[di]));
-  const unsigned gem = (unsigned)std::min<unsigned long long>((total_chunks + kBlock - 1) / kBlock,
-                                                               (unsigned long long)sd->num_sms * 32);
+  const unsigned gfi = std::min<unsigned>(total_fin, (unsigned)(sd->num_sms * sd->bpsm_final));
   ntab_kernel<<<dim3(256, 1), 256, 0, s>>>(ddesc, 1);
   if (p->satgrow) {
     const unsigned nw = (unsigned)((size_t)ny * wpr_of(nx));
@@ -952,10 +956,9 @@ extern "C" int lacos_run_static(const void* d_frame, lacos_dtype dt, int ny, int
   for (int k = 1; k <= p->niter; ++k) {
     if (h.gain_est) launch_gain_level(ddesc, 1, k, sd->num_sms, s);
     V.fn[di]<<<gd, V.nt, V.smem[di], s>>>(ddesc, 1, 0, total, k, heads + kHeadCore + di * kHeadLevels + k);
-    grow_kernel<<<(total_gblk + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(ddesc, 1, total_gblk, k);
+    grow_kernel<<<total_gblk, kBlock, 0, s>>>(ddesc, 1, total_gblk, k);
   }
-  emit_kernel<<<gem, kBlock, 0, s>>>(ddesc, 1, total_chunks);
-  replace_kernel<<<total_rblk, kBlock, 0, s>>>(ddesc, 1, total_rblk);
+  finalize_kernel<<<gfi, kBlock, 0, s>>>(ddesc, 1, total_fin, heads + kHeadFinal);
   if (cudaGetLastError() != cudaSuccess) return LACOS_ECUDA;
   FrameState hs;
   if (cudaMemcpyAsync(&hs, dstate, sizeof(FrameState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -20,8 +20,7 @@
 // reciprocal with two Markstein corrections (div_recip), and the dense
 // networks run on packed pairs.  With saturated-star protection the grown
 // saturated set is built once per request (satseed_kernel, satgrow_kernel).
-// emit_kernel and replace_kernel write the cleaned frame R(X0, M) and the
-// uint8 mask.
+// finalize_kernel writes the cleaned frame R(X0, M) and the uint8 mask.
 //
 // Every stage evaluates its own array at in-frame positions only and reads
 // out-of-frame neighbours at clamped coordinates (clamp-to-edge per stage).
@@ -96,12 +95,14 @@ struct Geo {
     __host__ __device__ static constexpr int idx(int ly, int lx) { return (ly + H) * W + (lx + C); }
   };
   using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
+  using XR3 = Reg<3, 8>;  // finalize
   static_assert(TW % 64 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
 };
-// The variants' tile shapes.
+// The variants' tile shapes.  Finalize always runs on 32 x 64 tiles.
 using G32x64 = Geo<32, 64, 256>;
 using G64x64 = Geo<64, 64, 512>;
 using G32x128 = Geo<32, 128, 512>;
+using FG = G32x64;
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -123,9 +124,11 @@ struct FrameState {
   int iters_run;
   // Gain estimation (frames with gain 0), per level: the range of d present
   // in the level's histogram as max(65535 - d) and max(d + 65535) over the
-  // pairs (0 and 0: no pair), the level whose core launch recomputes every
-  // tile (the gain changed), and the latest level's gain.
+  // pairs (0 and 0: no pair), the sums of the full pair set, the level whose
+  // core launch recomputes every tile (the gain changed), and the latest
+  // level's gain.
   unsigned int g_dneg, g_dpos;
+  unsigned long long g0[4];  // the level's full pair set: n, sum d (two's complement), sum d^2, sum (a + b)
   int g_all_level;
   float gain;
 };
@@ -156,8 +159,8 @@ struct FrameDesc {
   int th, tw;        // core tile shape of the request's core-kernel variant
   int tiles_x;       // core tiles per row
   unsigned int tile_begin, tile_end;    // this frame's range in the flattened core-tile list
-  unsigned long long chunk_begin;       // emit_kernel: this frame's first 8-pixel chunk
-  unsigned int rblk_begin;              // replace_kernel: this frame's first block of mask words
+  int ftiles_x;                         // finalize tiles (32 x 64) per row
+  unsigned int fin_begin, fin_end;      // this frame's range in the flattened finalize-tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
   unsigned int gblk_begin, gblk_x;      // growth items: this frame's first, column groups per strip
 };
@@ -225,6 +228,15 @@ __device__ __forceinline__ int frame_of(const FrameDesc* fr, int nframes, unsign
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (fr[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int frame_of_fin(const FrameDesc* fr, int nframes, unsigned item) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (fr[mid].fin_begin <= item) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -302,6 +314,37 @@ __device__ __forceinline__ bool maskmed5(const XT* X, const uint8_t* Mb, int P, 
     }
   K o;
   med5x5<K>(v, &o);
+  out = KT::back(o);
+  return true;
+}
+
+// Masked 7x7 median (the first widening): the same sentinel scheme with the
+// rank-24 element of 49.  Returns false when no member is unflagged.
+template <class XT>
+__device__ __forceinline__ bool maskmed7(const XT* X, const uint8_t* Mb, int P, int c, XT& out) {
+  using KT = KeyOf<XT>;
+  using K = typename KT::K;
+  int n = 0;
+#pragma unroll
+  for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) n += Mb[c + dy * P + dx] ? 0 : 1;
+  if (n == 0) return false;
+  const int plo = 24 - (n - 1) / 2;
+  K v[49];
+  int seen = 0;
+#pragma unroll
+  for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) {
+      const int q = c + dy * P + dx;
+      const bool fl = Mb[q] != 0;
+      const K s = (seen < plo) ? KT::lo() : KT::hi();
+      seen += fl ? 1 : 0;
+      v[(dy + 3) * 7 + dx + 3] = fl ? s : KT::key(X[q]);
+    }
+  K o;
+  med7x7<K>(v, &o);
   out = KT::back(o);
   return true;
 }
@@ -416,11 +459,15 @@ __global__ void __launch_bounds__(kBlock, 4) gain_hist_kernel(const FrameDesc* _
   const FrameDesc& f = fr[fi];
   FrameState* st = f.st;
   if (!f.gain_est || !iteration_runs(f, k)) return;
-  __shared__ unsigned int hn[2 * kGainSmemHalf];
-  __shared__ unsigned long long ha[2 * kGainSmemHalf];
+  // Shared bins: the count, and the sum of a + b as two 32-bit halves (a
+  // carry out of the low half is added to the high half by the thread whose
+  // addition wrapped, so the pair of words holds the exact 64-bit sum).
+  __shared__ unsigned int hn[2 * kGainSmemHalf], hlo[2 * kGainSmemHalf], hhi[2 * kGainSmemHalf];
+  __shared__ unsigned long long red[kBlock / 32][4];
   for (int i = threadIdx.x; i < 2 * kGainSmemHalf; i += kBlock) {
     hn[i] = 0u;
-    ha[i] = 0ull;
+    hlo[i] = 0u;
+    hhi[i] = 0u;
   }
   __syncthreads();
   const uint32_t* Mprev = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;  // M_(k-1)
@@ -431,6 +478,8 @@ __global__ void __launch_bounds__(kBlock, 4) gain_hist_kernel(const FrameDesc* _
   const unsigned nwords = (unsigned)f.ny * (unsigned)f.wpr;
   const uint16_t* x0 = static_cast<const uint16_t*>(f.x0);
   unsigned dneg = 0, dpos = 0;  // max(65535 - d), max(d + 65535) over this thread's pairs
+  unsigned long long n0 = 0, s20 = 0, a0 = 0;  // the full set's sums (clipping round 0)
+  long long s10 = 0;
   for (unsigned w = blockIdx.x * kBlock + threadIdx.x; w < nwords; w += gridDim.x * kBlock) {
     const int y = (int)(w / (unsigned)f.wpr), xw = (int)(w % (unsigned)f.wpr) * 32;
     const int cnt = min(32, f.nx - xw);  // pixels of this word
@@ -465,9 +514,15 @@ __global__ void __launch_bounds__(kBlock, 4) gain_hist_kernel(const FrameDesc* _
       const int d = va - vb;
       dneg = max(dneg, (unsigned)(65535 - d));
       dpos = max(dpos, (unsigned)(d + 65535));
+      n0 += 1;
+      s10 += d;
+      s20 += (unsigned long long)((long long)d * d);
+      a0 += (unsigned long long)(va + vb);
       if (d >= -kGainSmemHalf && d < kGainSmemHalf) {
-        atomicAdd(&hn[d + kGainSmemHalf], 1u);
-        atomicAdd(&ha[d + kGainSmemHalf], (unsigned long long)(va + vb));
+        const int i = d + kGainSmemHalf;
+        const unsigned ab = (unsigned)(va + vb);
+        atomicAdd(&hn[i], 1u);
+        if (atomicAdd(&hlo[i], ab) > 0xffffffffu - ab) atomicAdd(&hhi[i], 1u);
       } else {
         atomicAdd(&f.ghist_n[d + 65535], 1u);
         atomicAdd(&f.ghist_a[d + 65535], (unsigned long long)(va + vb));
@@ -476,15 +531,31 @@ __global__ void __launch_bounds__(kBlock, 4) gain_hist_kernel(const FrameDesc* _
   }
   dneg = __reduce_max_sync(0xffffffffu, dneg);
   dpos = __reduce_max_sync(0xffffffffu, dpos);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n0 += __shfl_down_sync(0xffffffffu, n0, o);
+    s10 += __shfl_down_sync(0xffffffffu, s10, o);
+    s20 += __shfl_down_sync(0xffffffffu, s20, o);
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+  }
   if ((threadIdx.x & 31) == 0) {
     if (dneg) atomicMax(&st->g_dneg, dneg);
     if (dpos) atomicMax(&st->g_dpos, dpos);
+    red[threadIdx.x >> 5][0] = n0;
+    red[threadIdx.x >> 5][1] = (unsigned long long)s10;
+    red[threadIdx.x >> 5][2] = s20;
+    red[threadIdx.x >> 5][3] = a0;
   }
   __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long t = 0;
+    for (int q = 0; q < kBlock / 32; ++q) t += red[q][threadIdx.x];
+    if (t) atomicAdd(&st->g0[threadIdx.x], t);
+  }
   for (int i = threadIdx.x; i < 2 * kGainSmemHalf; i += kBlock) {
     if (!hn[i]) continue;
     atomicAdd(&f.ghist_n[i - kGainSmemHalf + 65535], hn[i]);
-    atomicAdd(&f.ghist_a[i - kGainSmemHalf + 65535], ha[i]);
+    atomicAdd(&f.ghist_a[i - kGainSmemHalf + 65535], ((unsigned long long)hhi[i] << 32) | hlo[i]);
   }
 }
 
@@ -515,9 +586,17 @@ __global__ void __launch_bounds__(kFoldThreads) gain_fold_kernel(const FrameDesc
   }
   __syncthreads();
   for (int r = 0; r < kGainRounds; ++r) {
-    const long long lo = max(s_lo, (long long)dlo), hi = min(s_hi, (long long)dhi);
+    // Round 0 takes every pair: its sums came with the histogram.
+    const long long lo = r == 0 ? 1 : max(s_lo, (long long)dlo), hi = r == 0 ? 0 : min(s_hi, (long long)dhi);
     unsigned long long n = 0, s2 = 0, a = 0;
     long long s1 = 0;
+    if (r == 0 && threadIdx.x < 4) {
+      const unsigned long long t = __ldcg(&st->g0[threadIdx.x]);
+      if (threadIdx.x == 0) n = t;
+      if (threadIdx.x == 1) s1 = (long long)t;
+      if (threadIdx.x == 2) s2 = t;
+      if (threadIdx.x == 3) a = t;
+    }
     for (long long d = lo + threadIdx.x; d <= hi; d += kFoldThreads) {
       const unsigned long long c = __ldcg(&f.ghist_n[d + 65535]);
       if (!c) continue;
@@ -573,6 +652,7 @@ __global__ void __launch_bounds__(kFoldThreads) gain_fold_kernel(const FrameDesc
     f.ghist_n[d + 65535] = 0u;
     f.ghist_a[d + 65535] = 0ull;
   }
+  if (threadIdx.x < 4) st->g0[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
     st->g_dneg = 0u;
     st->g_dpos = 0u;
@@ -1396,15 +1476,18 @@ __device__ __forceinline__ void mark_tiles(const FrameDesc& f, int kn, int y, in
 
 // ---- step 6: growth on 32-pixel words --------------------------------------
 
-// Growth work items: one warp covers a strip of kGrowRows rows of 32
-// consecutive mask words and writes the middle kGrowOut of them (the two
-// words on each side are the halo the two 3x3 dilations need).  Each lane
-// walks its word down the strip, dilating vertically in registers and
-// horizontally with its neighbours' words by shuffles: no shared memory and
-// no barrier.  Items are numbered per frame from gblk_begin: gblk_x column
-// groups per strip, strips top to bottom.
-constexpr int kGrowRows = 16;
-constexpr int kGrowOut = 28;
+__device__ __forceinline__ uint32_t plane_word(const uint32_t* P, int ny, int wpr, int y, int w) {
+  if (y < 0 || y >= ny || w < 0 || w >= wpr) return 0u;
+  return __ldg(P + (size_t)y * wpr + w);
+}
+
+// Horizontal 3-dilation of word c with the edge bits of its neighbours.
+__device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
+  return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
+}
+
+constexpr int GB_H = 32, GB_W = 8;  // growth block: 32 rows x 8 words (one word per thread)
+static_assert(GB_H * GB_W == kBlock, "one word per thread");
 
 __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, unsigned b) {
   int lo = 0, hi = nframes - 1;
@@ -1415,255 +1498,214 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
   return lo;
 }
 
-// Step 6 on one strip: g1 = dil3(cand) & sig, g2 = dil3(g1) & lo (both
-// excluding saturated pixels, which the planes already do), M_k = M_(k-1) |
-// g2, whether the level found new pixels, and the tiles the next level must
-// recompute.  Out-of-frame words read as zero (dilation treats the outside
-// as unflagged).
+// Step 6 for a block of 32 rows x 8 words: the candidate words (with a
+// 2-row, 2-word halo) and the first growth g1 = dil3(cand) & sig (1-row,
+// 1-word halo) are staged in shared memory; each thread then forms
+// g2 = dil3(g1) & lo for its word, M_k = M_{k-1} | g2, and counts new flags.
+// Every global load of the block (candidate, sig, lo and mask words) is
+// issued up front, so the block waits for one memory round trip.
 __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                      unsigned total_items, int k) {
-  const int lane = threadIdx.x & 31;
-  const unsigned item = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
-  if (item >= total_items) return;  // whole warps leave together
-  const FrameDesc& f = fr[frame_of_gblk(fr, nframes, item)];
+                                                      unsigned total_blocks, int k) {
+  constexpr int NT = kBlock;
+  constexpr int CW = GB_W + 4, CN = (GB_H + 4) * CW;  // candidate region
+  constexpr int GW = GB_W + 2, GN = (GB_H + 2) * GW;  // g1 region
+  constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
+  __shared__ uint32_t C[GB_H + 4][CW];
+  __shared__ uint32_t G1[GB_H + 2][GW];
+  const int tid = threadIdx.x;
+  const unsigned blk = blockIdx.x;
+  if (blk >= total_blocks) return;
+  const FrameDesc& f = fr[frame_of_gblk(fr, nframes, blk)];
   if (!iteration_runs(f, k)) return;
-  const unsigned b = item - f.gblk_begin;
-  const int y0 = (int)(b / (unsigned)f.gblk_x) * kGrowRows;
-  const int w = (int)(b % (unsigned)f.gblk_x) * kGrowOut - 2 + lane;  // this lane's word
+  const unsigned b = blk - f.gblk_begin;
+  const int y0 = (int)(b / (unsigned)f.gblk_x) * GB_H, w0 = (int)(b % (unsigned)f.gblk_x) * GB_W;
   const int ny = f.ny, wpr = f.wpr;
-  const bool wok = w >= 0 && w < wpr;
-  const bool out = lane >= 2 && lane < 2 + kGrowOut && wok;  // lanes that write their word
+  const int ty = tid / GB_W, tx = tid % GB_W;
+  const int y = y0 + ty, w = w0 + tx;
+  const bool own = y < ny && w < wpr;
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
-  uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
-  const auto word = [&](const uint32_t* P, int y) -> uint32_t {
-    return (wok && y >= 0 && y < ny) ? __ldg(P + (size_t)y * wpr + w) : 0u;
-  };
-  const auto hd = [&](uint32_t c) {  // horizontal 3-dilation with the neighbouring lanes' words
-    const uint32_t l = __shfl_up_sync(0xffffffffu, c, 1), r = __shfl_down_sync(0xffffffffu, c, 1);
-    return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
-  };
-  // Sliding windows: hc = horizontally dilated candidates of rows y-1, y, y+1
-  // (for g1 at row y), hg = horizontally dilated g1 of rows y-1, y, y+1 (for g2).
-  uint32_t hc0 = hd(word(f.p_cand, y0 - 2)), hc1 = hd(word(f.p_cand, y0 - 1));
-  uint32_t hg0 = 0u, hg1 = 0u;
-  bool any = false;
-  // Row r of the loop produces g1 at row y0 - 1 + r and, from r >= 2, g2 at row y0 + r - 2.
-  for (int r = 0; r < kGrowRows + 2; ++r) {
-    const int yc = y0 + r;        // candidate row entering the window
-    const int yg = y0 - 1 + r;    // g1 row completed
-    const uint32_t hc2 = hd(word(f.p_cand, yc));
-    const uint32_t g1 = (hc0 | hc1 | hc2) & word(f.p_sig, yg);
-    const uint32_t hg2 = hd(g1);
-    if (r >= 2) {
-      const int y = y0 + r - 2;   // output row: g1 rows y-1, y, y+1 are hg0, hg1, hg2
-      if (y < ny) {
-        const uint32_t g2 = (hg0 | hg1 | hg2) & word(f.p_lo, y);
-        if (out) {
-          const uint32_t mp = word(Mp, y);
-          Mn[(size_t)y * wpr + w] = mp | g2;
-          const uint32_t fresh = g2 & ~mp;
-          if (fresh) {
-            any = true;
-            if (k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
-          }
-        }
-      }
+  uint32_t cw[CP], sw[GP];
+#pragma unroll
+  for (int p = 0; p < CP; ++p) {
+    const int i = p * NT + tid;
+    cw[p] = i < CN ? plane_word(f.p_cand, ny, wpr, y0 - 2 + i / CW, w0 - 2 + i % CW) : 0u;
+  }
+#pragma unroll
+  for (int p = 0; p < GP; ++p) {
+    const int i = p * NT + tid;
+    sw[p] = i < GN ? plane_word(f.p_sig, ny, wpr, y0 - 1 + i / GW, w0 - 1 + i % GW) : 0u;
+  }
+  const uint32_t lo = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
+  const uint32_t mp = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
+#pragma unroll
+  for (int p = 0; p < CP; ++p) {
+    const int i = p * NT + tid;
+    if (i < CN) C[i / CW][i % CW] = cw[p];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < GP; ++p) {
+    const int i = p * NT + tid;
+    if (i < GN) {
+      const int r = i / GW, c = i % GW;
+      uint32_t d = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][c], C[r + a][c + 1], C[r + a][c + 2]);
+      G1[r][c] = d & sw[p];
     }
-    hc0 = hc1;
-    hc1 = hc2;
-    hg0 = hg1;
-    hg1 = hg2;
+  }
+  __syncthreads();
+  bool any = false;
+  if (own) {
+    uint32_t d2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d2 |= hdil(G1[ty + a][tx], G1[ty + a][tx + 1], G1[ty + a][tx + 2]);
+    const uint32_t g2 = d2 & lo;
+    uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
+    Mn[(size_t)y * wpr + w] = mp | g2;
+    const uint32_t fresh = g2 & ~mp;
+    any = fresh != 0;
+    if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
   }
   // Only "did level k flag anything" is used (early stop): one flag store
-  // per warp that found new pixels, skipped once some warp has set it.
-  if (__any_sync(0xffffffffu, any) && lane == 0 && !*(volatile unsigned long long*)&f.st->fresh[k])
+  // per block that found new pixels, skipped once some block has set it.
+  if (__syncthreads_or(any) && tid == 0 && !*(volatile unsigned long long*)&f.st->fresh[k])
     f.st->fresh[k] = 1;
 }
 
 // ---- output: cleaned frame and uint8 mask of the last mask ----------------
-//
-// Two passes.  emit_kernel streams the whole frame: cleaned = X0 and mask =
-// M_run as bytes, eight pixels per thread (16-byte rows: one 16- or 32-byte
-// load, two 16-byte stores and one 8-byte store).  replace_kernel then walks
-// M_run word by word and overwrites the cleaned value of each flagged pixel
-// with its masked median (step 7 of the last iteration run), reading X0 and
-// the mask words from global memory (L1-cached: a flagged pixel's window is
-// shared with its flagged neighbours).
 
-constexpr int kEmitPx = 8;  // pixels per thread and step in emit_kernel
-
-__device__ __forceinline__ int frame_of_u64(const FrameDesc* fr, int nframes, unsigned long long v,
-                                            unsigned long long FrameDesc::*begin) {
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (fr[mid].*begin <= v) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Grid-stride over the flattened 8-pixel chunks of every frame (chunk_begin:
-// this frame's first chunk; a frame has ny * ceil(nx / 8) of them).
-__global__ void __launch_bounds__(kBlock) emit_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                      unsigned long long total_chunks) {
-  for (unsigned long long q = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; q < total_chunks;
-       q += (unsigned long long)gridDim.x * kBlock) {
-    const FrameDesc& f = fr[nframes > 1 ? frame_of_u64(fr, nframes, q, &FrameDesc::chunk_begin) : 0];
-    const unsigned long long c = q - f.chunk_begin;
-    const int cpr = (f.nx + kEmitPx - 1) / kEmitPx;  // chunks per row
-    const int y = (int)(c / (unsigned)cpr), x = (int)(c % (unsigned)cpr) * kEmitPx;
-    const int run = run_of(f);
-    const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
-    const uint32_t bits = (__ldg(M + (size_t)y * f.wpr + (x >> 5)) >> (x & 31)) & 0xffu;
-    const size_t p = (size_t)y * f.nx + x;
-    // Whole, aligned chunks: rows of a multiple of 8 pixels and 16-byte aligned buffers.
-    const bool vec = (f.nx % kEmitPx) == 0 && (reinterpret_cast<uintptr_t>(f.x0) & 15u) == 0 &&
-                     (reinterpret_cast<uintptr_t>(f.clean_out) & 15u) == 0 &&
-                     (reinterpret_cast<uintptr_t>(f.mask_out) & 7u) == 0;
-    if (vec) {
-      float v[8];
-      if (f.dtype == 1) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(f.x0) + p));
-        const uint32_t h[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = (float)((h[e >> 1] >> (16 * (e & 1))) & 0xffffu);
-      } else {
-        const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(f.x0) + p);
-        const float4 a = __ldg(src), b = __ldg(src + 1);
-        const float w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        bool bad = false;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          float t = w[e];
-          if (!isfinite(t)) { bad = true; t = 0.0f; }
-          v[e] = t == 0.0f ? 0.0f : t;  // -0 -> +0
-        }
-        if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
-      }
-      float4* dst = reinterpret_cast<float4*>(f.clean_out + p);
-      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-      // bit t -> byte t (the multiply moves bit t of a 4-bit group to bit 8t; no carries)
-      *reinterpret_cast<uint2*>(f.mask_out + p) = make_uint2(((bits & 0xfu) * 0x00204081u) & 0x01010101u,
-                                                             (((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u);
-    } else {
-      bool bad = false;
-      for (int e = 0; e < kEmitPx && x + e < f.nx; ++e) {
-        f.clean_out[p + e] = load_x0(f, y, x + e, bad);
-        f.mask_out[p + e] = (uint8_t)((bits >> e) & 1u);
-      }
-      if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
-    }
-  }
-}
-
-// Masked 5x5 median of pixel (gy, gx) straight from global memory: the
-// lower median of the unflagged original values of the clamped window, by
-// the sentinel network of maskmed5; false when every member is flagged.
 template <class XT>
-__device__ __forceinline__ bool maskmed5_global(const FrameDesc& f, const uint32_t* M, int gy, int gx, float& out) {
-  using KT = KeyOf<XT>;
-  using K = typename KT::K;
-  uint32_t fl = 0;  // bit i: window member i is flagged
-  int rows[5], cols[5];
-#pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    rows[t] = clampi(gy + t - 2, 0, f.ny - 1);
-    cols[t] = clampi(gx + t - 2, 0, f.nx - 1);
-  }
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) fl |= mask_bit(M, f.wpr, rows[a], cols[b]) << (a * 5 + b);
-  const int n = 25 - __popc(fl);
-  if (n == 0) return false;
-  const int plo = 12 - (n - 1) / 2;
-  K v[25];
-  int seen = 0;
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int i = a * 5 + b;
-      const bool flg = (fl >> i) & 1u;
-      const K sentinel = (seen < plo) ? KT::lo() : KT::hi();
-      seen += flg ? 1 : 0;
-      K key;
-      if (flg) {
-        key = sentinel;
-      } else if constexpr (std::is_same<XT, uint16_t>::value) {
-        key = (K)__ldg(static_cast<const uint16_t*>(f.x0) + (size_t)rows[a] * f.nx + cols[b]);
-      } else {
-        bool bad = false;
-        key = (K)load_x0(f, rows[a], cols[b], bad);
-      }
-      v[i] = key;
-    }
-  K o;
-  med5x5<K>(v, &o);
-  out = (float)KT::back(o);
-  return true;
+struct FinalSmemT {
+  XT X[FG::XR3::N];
+  uint8_t Mb[FG::XR3::N];
+  uint32_t Mw[FG::TH + 6][FG::MWORDS];
+  uint16_t list[FG::TH * FG::TW];
+  unsigned nlist;
+};
+constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
+
+// The rare replacements whose 5x5 window is fully flagged: the 7x7 window
+// from shared memory, else wider windows from global memory.  Kept out of
+// line so that the common path's register allocation does not carry the
+// 49-key network.
+template <class XT>
+__device__ __noinline__ XT replace_wide(const FrameDesc& f, const uint32_t* M, const FinalSmemT<XT>& sm, int c,
+                                        int gy, int gx) {
+  XT v;
+  if (!maskmed7(sm.X, sm.Mb, FG::XR3::W, c, v)) v = (XT)maskmed_wide(f, M, gy, gx, 4);
+  return v;
 }
 
-// Blocks of kBlock consecutive mask words of one frame (rblk_begin: this
-// frame's first block): the flagged pixels of the block's words are listed
-// in shared memory (one prefix sum), then replaced one per thread.  The
-// block also adds its flagged count to the frame's, and the frame's first
-// block records the iterations run.
-__global__ void __launch_bounds__(kBlock) replace_kernel(const FrameDesc* __restrict__ fr, int nframes,
-                                                         unsigned total_blocks) {
-  __shared__ uint16_t list[kBlock * 32];
-  __shared__ unsigned warp_base[kBlock / 32 + 1];
-  const unsigned blk = blockIdx.x;
-  if (blk >= total_blocks) return;
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (fr[mid].rblk_begin <= blk) lo = mid; else hi = mid - 1;
-  }
-  const FrameDesc& f = fr[lo];
+// cleaned = R(X0, M_run) (the masked median at flagged pixels, X0 elsewhere),
+// mask = M_run as uint8, the flagged count and the iterations run.  The
+// flagged pixels of a tile are compacted into a list, replaced in shared
+// memory, and the tile is then written out coalesced, four pixels per
+// thread where the row pitch allows 16-byte stores.
+template <class XT>
+__device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
+  constexpr int TH = FG::TH, TW = FG::TW, TWW = FG::TWW, NT = kBlock;
+  using XR3 = FG::XR3;
+  static_assert(FG::NT == kBlock, "finalize geometry");
+  const int tid = threadIdx.x;
+  const int oy = (tix / f.ftiles_x) * TH, ox = (tix % f.ftiles_x) * TW;
   const int run = run_of(f);
   const uint32_t* M = (run & 1) ? f.mbuf1 : f.mbuf0;
-  const unsigned nwords = (unsigned)f.ny * (unsigned)f.wpr;
-  const unsigned w0 = (blk - f.rblk_begin) * kBlock;
-  const unsigned w = w0 + threadIdx.x;
-  const uint32_t bits = w < nwords ? __ldg(M + w) : 0u;  // bits beyond the frame are never set
-  // Exclusive prefix sum of the per-word counts over the block.
-  const unsigned c = __popc(bits);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_base[wid] = incl;
+  bool bad = false;
+  stage_x0_mask<FG, 3>(f, M, oy, ox, sm.X, sm.Mb, sm.Mw, bad);
+  if (bad) atomicOr(&f.st->err, ERR_NONFINITE);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned acc = 0;
-    for (int i = 0; i < kBlock / 32; ++i) {
-      const unsigned t = warp_base[i];
-      warp_base[i] = acc;
-      acc += t;
+  // The tile's flagged pixels straight from the staged mask words (the
+  // tile's columns are whole words; bits beyond the frame are never set):
+  // the first two warps, one word each, one shared atomic per warp.
+  static_assert(TH * TWW % 32 == 0 && TH * TWW <= NT, "whole warps of mask words");
+  if (tid < TH * TWW) {
+    const int ly = tid / TWW, wd = tid % TWW;
+    const int w0 = clampi(ox - 8, 0, f.nx - 1) >> 5;  // as staged
+    const uint32_t bits = (oy + ly) < f.ny ? sm.Mw[ly + 3][((ox >> 5) + wd) - w0] : 0u;
+    warp_emit(bits, &sm.nlist, sm.list, -1, [&](int b) { return (uint16_t)(ly * TW + wd * 32 + b); });
+  }
+  __syncthreads();
+  const unsigned n = sm.nlist;
+  // In place: reads touch unflagged pixels only, writes flagged ones.
+  for (unsigned j = tid; j < n; j += NT) {
+    const int i = sm.list[j];
+    const int ly = i / TW, lx = i % TW;
+    const int c = XR3::idx(ly, lx);
+    XT v;
+    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v)) v = replace_wide(f, M, sm, c, oy + ly, ox + lx);
+    sm.X[c] = v;
+  }
+  __syncthreads();
+  const bool vec = (f.nx & 3) == 0;
+  for (int qd = tid; qd < TH * TW / 4; qd += NT) {
+    const int ly = qd / (TW / 4), lx = (qd % (TW / 4)) * 4;
+    const int gy = oy + ly, gx = ox + lx;
+    if (gy >= f.ny || gx >= f.nx) continue;
+    const int c = XR3::idx(ly, lx);
+    const size_t q = (size_t)gy * f.nx + gx;
+    if (vec && gx + 3 < f.nx) {  // c is a multiple of 4: aligned shared-memory reads
+      float4 o;
+      if constexpr (std::is_same<XT, float>::value) {
+        o = *reinterpret_cast<const float4*>(sm.X + c);
+      } else {
+        const uint2 u = *reinterpret_cast<const uint2*>(sm.X + c);
+        o = make_float4((float)(u.x & 0xffffu), (float)(u.x >> 16), (float)(u.y & 0xffffu), (float)(u.y >> 16));
+      }
+      *reinterpret_cast<float4*>(f.clean_out + q) = o;
+      *reinterpret_cast<uint32_t*>(f.mask_out + q) = *reinterpret_cast<const uint32_t*>(sm.Mb + c);
+    } else {
+      for (int e = 0; e < 4 && gx + e < f.nx; ++e) {
+        f.clean_out[q + e] = (float)sm.X[c + e];
+        f.mask_out[q + e] = sm.Mb[c + e];
+      }
     }
-    warp_base[kBlock / 32] = acc;
-    if (acc) atomicAdd(&f.st->flagged, (unsigned long long)acc);
-    if (blk == f.rblk_begin) f.st->iters_run = run;
   }
-  __syncthreads();
-  unsigned pos = warp_base[wid] + incl - c;
-  for (uint32_t b = bits; b; b &= b - 1u) list[pos++] = (uint16_t)((threadIdx.x << 5) | (__ffs(b) - 1));
-  __syncthreads();
-  const unsigned n = warp_base[kBlock / 32];
-  for (unsigned j = threadIdx.x; j < n; j += kBlock) {
-    const unsigned e = list[j];
-    const unsigned wi = w0 + (e >> 5);
-    const int gy = (int)(wi / (unsigned)f.wpr), gx = (int)(wi % (unsigned)f.wpr) * 32 + (int)(e & 31u);
-    float v;
-    const bool ok = f.dtype == 1 ? maskmed5_global<uint16_t>(f, M, gy, gx, v) : maskmed5_global<float>(f, M, gy, gx, v);
-    if (!ok) v = maskmed_wide(f, M, gy, gx, 3);
-    f.clean_out[(size_t)gy * f.nx + gx] = v;
+  if (tid == 0 && tix == 0) f.st->iters_run = run;
+  return n;
+}
+
+__global__ void __launch_bounds__(kBlock, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
+                                                         unsigned total, unsigned* head) {
+  __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
+  __shared__ unsigned s_item;
+  const int tid = threadIdx.x;
+  __shared__ unsigned long long flagged;  // flagged pixels of frame acc_st so far (thread 0)
+  __shared__ FrameState* acc_st;
+  if (tid == 0) {
+    flagged = 0;
+    acc_st = nullptr;
   }
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(head, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= total) break;
+    const FrameDesc& f = fr[frame_of_fin(fr, nframes, item)];
+    const int tix = (int)(item - f.fin_begin);
+    unsigned n;
+    if (f.dtype == 1) {
+      auto& sm = *reinterpret_cast<FinalSmemT<uint16_t>*>(smem);
+      if (tid == 0) sm.nlist = 0;
+      __syncthreads();
+      n = finalize_tile<uint16_t>(f, tix, sm);
+    } else {
+      auto& sm = *reinterpret_cast<FinalSmemT<float>*>(smem);
+      if (tid == 0) sm.nlist = 0;
+      __syncthreads();
+      n = finalize_tile<float>(f, tix, sm);
+    }
+    if (tid == 0) {
+      if (f.st != acc_st) {
+        if (acc_st && flagged) atomicAdd(&acc_st->flagged, flagged);
+        flagged = 0;
+        acc_st = f.st;
+      }
+      flagged += n;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && acc_st && flagged) atomicAdd(&acc_st->flagged, flagged);
 }
 
 }  // namespace lacos
