@@ -33,7 +33,7 @@ WORKLOAD = "lacosmic_9576x6388_u16_niter4"
 # DRAM bytes (read + write) per core_kernel launch from one ncu capture on
 # this workload, keyed by kernel_source_sha() of the captured build; any other
 # source reports null (the counters no longer describe the kernel).
-NCU_CORE_TRAFFIC = {"f6175d2fa2a59759": 149_255_936}
+NCU_CORE_TRAFFIC = {"6a0257744c9513d9": 131_703_552 + 17_389_824}
 
 
 def kernel_source_sha() -> str:

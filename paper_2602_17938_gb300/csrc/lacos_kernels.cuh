@@ -362,12 +362,6 @@ __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t
   constexpr int C = 8;
   const int ny = f.ny, nx = f.nx;
   const int w0 = clampi(ox - C, 0, nx - 1) >> 5;
-  for (int i = threadIdx.x; i < (TH + 2 * H) * MWORDS; i += NT) {
-    const int r = i / MWORDS, w = w0 + i % MWORDS;
-    const int gy = clampi(oy - H + r, 0, ny - 1);
-    Mw[r][i % MWORDS] = w < f.wpr ? __ldg(M + (size_t)gy * f.wpr + w) : 0u;
-  }
-  __syncthreads();
   // Columns ox-8 .. ox+TW+7 all inside the frame, rows 16-byte aligned:
   // 16-byte loads of 16 / sizeof(XT) pixels (rows are still clamped).
   constexpr int V = 16 / (int)sizeof(XT);  // pixels per 16-byte chunk
@@ -375,29 +369,49 @@ __device__ __forceinline__ void stage_x0_mask(const FrameDesc& f, const uint32_t
   static_assert(R::W % V == 0 && C % V == 0 && (32 % V) == 0, "chunking");
   const bool vec = ((reinterpret_cast<uintptr_t>(f.x0) & 15u) == 0) && (nx % V == 0) && ox - C >= 0 &&
                    ox + TW + C <= nx;
+  // Interior tiles: the rows are copied asynchronously (16-byte cp.async),
+  // in flight while the mask words load and their bits are spread.
   if (vec) {
     for (int i = threadIdx.x; i < (TH + 2 * H) * CPR; i += NT) {
       const int r = i / CPR, q = i % CPR;
       const int gy = clampi(oy - H + r, 0, ny - 1);
+      const XT* src = static_cast<const XT*>(f.x0) + (size_t)gy * nx + (ox - C + q * V);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(X + r * R::W + q * V);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < (TH + 2 * H) * MWORDS; i += NT) {
+    const int r = i / MWORDS, w = w0 + i % MWORDS;
+    const int gy = clampi(oy - H + r, 0, ny - 1);
+    Mw[r][i % MWORDS] = w < f.wpr ? __ldg(M + (size_t)gy * f.wpr + w) : 0u;
+  }
+  __syncthreads();
+  if (vec) {
+    for (int i = threadIdx.x; i < (TH + 2 * H) * CPR; i += NT) {
+      const int r = i / CPR, q = i % CPR;
       const int gx = ox - C + q * V;
-      const XT* src = static_cast<const XT*>(f.x0) + (size_t)gy * nx + gx;
-      const int c = r * R::W + q * V;
       const uint32_t bits = Mw[r][(gx >> 5) - w0] >> (gx & 31);
-      if constexpr (std::is_same<XT, float>::value) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(src));
+      // V mask bits -> V bytes (bit t moves to bit 8t by the multiply; no carries)
+      if constexpr (std::is_same<XT, float>::value)
+        *reinterpret_cast<uint32_t*>(Mb + r * R::W + q * V) = ((bits & 0xfu) * 0x00204081u) & 0x01010101u;
+      else
+        *reinterpret_cast<uint2*>(Mb + r * R::W + q * V) = make_uint2(((bits & 0xfu) * 0x00204081u) & 0x01010101u,
+                                                                 (((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies; the caller's barrier publishes them
+    if constexpr (std::is_same<XT, float>::value) {
+      // float input: canonicalise -0 and flag non-finite values in the chunks this thread copied
+      for (int i = threadIdx.x; i < (TH + 2 * H) * CPR; i += NT) {
+        float4* p = reinterpret_cast<float4*>(X + (i / CPR) * R::W + (i % CPR) * V);
+        const float4 v = *p;
         float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           if (!isfinite(e[t])) { bad = true; e[t] = 0.0f; }
           e[t] = e[t] == 0.0f ? 0.0f : e[t];  // -0 -> +0
         }
-        *reinterpret_cast<float4*>(X + c) = make_float4(e[0], e[1], e[2], e[3]);
-        // 4 mask bits -> 4 bytes (bit t moves to bit 8t; no carries between them).
-        *reinterpret_cast<uint32_t*>(Mb + c) = ((bits & 0xfu) * 0x00204081u) & 0x01010101u;
-      } else {
-        *reinterpret_cast<uint4*>(X + c) = __ldg(reinterpret_cast<const uint4*>(src));
-        *reinterpret_cast<uint2*>(Mb + c) = make_uint2(((bits & 0xfu) * 0x00204081u) & 0x01010101u,
-                                                       (((bits >> 4) & 0xfu) * 0x00204081u) & 0x01010101u);
+        *p = make_float4(e[0], e[1], e[2], e[3]);
       }
     }
     return;
