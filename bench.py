@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--stress", action="store_true",
+                    help="also run the plain/overlapped/batched comparison on the 32-frame stress subset")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small profiling case (every kernel of the library once per level) and exit")
     ap.add_argument("--serving-full", action="store_true",
@@ -309,18 +311,21 @@ def run_batched(args, dev, cpu_cores=None):
     from paper_2602_17938_gb300 import lacos, synth
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, specs in (("mixed64", synth.config_specs(2)),
-                        ("dense8", [synth.FrameSpec(**{**synth.config_specs(1)[0].__dict__, "seed": (1, i)})
-                                    for i in range(8)])):
+    sets = [("mixed64", synth.config_specs(2)),
+            ("dense8", [synth.FrameSpec(**{**synth.config_specs(1)[0].__dict__, "seed": (1, i)})
+                        for i in range(8)])]
+    if args.stress:
+        sets.append(("stress32", synth.config_specs(4)[::8]))
+    for name, specs in sets:
         t0 = time.perf_counter()
         frames = synth.make_frames_parallel(specs)
         gen_s = time.perf_counter() - t0
-        if name == "mixed64" and cpu_cores is not None:
+        if name in ("mixed64", "stress32") and cpu_cores is not None:
             rng = np.random.default_rng(2)
             jobs = []
             for f, sp in zip(frames, specs):
                 jobs += crop_jobs(f, sp, 2, 512, rng)
-            out["_oracle_jobs"] = jobs
+            out["_oracle_jobs" if name == "mixed64" else "_oracle_jobs_stress"] = jobs
         d_frames = [lacos.to_device(f, dev) for f in frames]
         del frames
         masks = [torch.empty(f.shape, dtype=torch.uint8, device=dev) for f in d_frames]
@@ -346,7 +351,44 @@ def run_batched(args, dev, cpu_cores=None):
                                   "(seed 2, 200 tracks per 512^2), niter=4")
     out["dense8"]["workload"] = ("8 frames of the 9576x6388 u16 recipe (seeds (1, 0..7): 150000 tracks, "
                                  "0.5% salt-and-pepper), niter=4")
+    if args.stress:
+        out["stress32"]["workload"] = ("every 8th of the 256 stress frames: 32 x 9576x6388 u16 (seed 4, 750000 "
+                                       "tracks, 1% salt-and-pepper, saturated stars, niter 1/4/6)")
     out["l2"] = "inputs (1-4.6 GB) far exceed L2"
+    return out
+
+
+def run_small_frame(args, dev, with_oracle):
+    """The 512 x 512 float32 frame of the first workload (seed 0), plain one frame
+    per call: device time per request (L2 not flushed: the frame is 1 MB), and
+    the oracle on the same whole frame on one host core."""
+    import torch
+    from paper_2602_17938_gb300 import lacos, synth
+    spec = synth.config_specs(0)[0]
+    frame = synth.make_frame(spec)
+    d = lacos.to_device(frame, dev)
+    m = torch.empty(frame.shape, dtype=torch.uint8, device=dev)
+    c = torch.empty(frame.shape, dtype=torch.float32, device=dev)
+    p = lacos.make_params(spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac, spec.objlim,
+                          spec.niter)
+    stream = torch.cuda.current_stream(dev)
+    with lacos.Context(dev.index or 0) as ctx:
+        def one():
+            ctx.wait(ctx.submit(d, p, m, c, stream))
+        ms = _time_passes(one, 50, stream)
+        r = ctx.wait(ctx.submit(d, p, m, c, stream))
+    out = {"workload": "512x512 f32 (seed 0: 20 stars, 200 tracks, 0.1% hot pixels), niter=4, one frame per call",
+           "ms_per_request": ms, "mpix_per_s": spec.npix / 1e6 / (ms / 1e3), "n_flagged": r.n_flagged,
+           "iters_run": r.iters_run, "l2": "not flushed (the frame and outputs are 6 MB)"}
+    if with_oracle:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.run(frame, spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac, spec.objlim,
+                   spec.niter)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": spec.npix / 1e6 / dt, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the whole frame, single-threaded float32 C++ oracle, {dt:.1f} s"}
     return out
 
 
@@ -546,12 +588,20 @@ def run_ours(args):
     batched = serving = None
     if ws == 1 and not args.no_batched:
         batched = run_batched(args, dev, cpu_cores=None if args.no_cpu_baseline else os.cpu_count())
+    small = run_small_frame(args, dev, not args.no_cpu_baseline) if ws == 1 else None
     if ws == 1 and not args.no_serving:
         serving = run_serving(args, dev)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else oracle_sample(frame, spec)
     cpu_nproc = None
+    if batched and "_oracle_jobs_stress" in batched:
+        jobs = batched.pop("_oracle_jobs_stress")
+        v, dt, cores = oracle_sample_nproc(jobs)
+        batched["stress32"]["cpu_baseline_nproc"] = {
+            "value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(jobs)} crops of 512x512 px, two from each of the 32 stress frames, one per process, "
+                      f"{dt:.1f} s wall"}
     if batched and "_oracle_jobs" in batched:
         jobs = batched.pop("_oracle_jobs")
         v, dt, cores = oracle_sample_nproc(jobs)
@@ -605,6 +655,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if cpu_nproc:
         line["cpu_baseline_nproc"] = cpu_nproc
+    if small:
+        line["small_frame"] = small
     print(json.dumps(line), flush=True)
 
 
