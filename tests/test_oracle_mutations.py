@@ -76,13 +76,29 @@ def source():
         return f.read()
 
 
-def test_unchanged_copy_passes_the_pins(source, tmp_path):
-    rc, out = _pins(_build(source, str(tmp_path / "same.so")))
+@pytest.fixture(scope="module")
+def outcomes(source, tmp_path_factory):
+    """Every copy (the unchanged one first) built and run against the pins, several at a
+    time (each is a compiler and a pytest process of its own)."""
+    from concurrent.futures import ThreadPoolExecutor
+    d = tmp_path_factory.mktemp("slips")
+    texts = [("unchanged", source)] + [(name, source.replace(old, new)) for name, old, new in SLIPS]
+
+    def one(i_text):
+        i, (name, text) = i_text
+        return name, _pins(_build(text, str(d / f"copy{i}.so")))
+
+    with ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(one, enumerate(texts)))
+
+
+def test_unchanged_copy_passes_the_pins(outcomes):
+    rc, out = outcomes["unchanged"]
     assert rc == 0, out
 
 
 @pytest.mark.parametrize("name,old,new", SLIPS, ids=[s[0] for s in SLIPS])
-def test_planted_slip_is_caught(source, tmp_path, name, old, new):
+def test_planted_slip_is_caught(source, outcomes, name, old, new):
     assert source.count(old) == 1, f"the text of '{name}' no longer occurs once in the oracle"
-    rc, out = _pins(_build(source.replace(old, new), str(tmp_path / "slip.so")))
+    rc, out = outcomes[name]
     assert rc != 0 and "failed" in out, f"slip not caught: {name}\n{out}"
