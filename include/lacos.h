@@ -27,7 +27,7 @@
  * Ownership: the caller owns frames and outputs and keeps them alive and
  * untouched from submit until poll reports completion.  The library owns
  * its scratch (5 bits per pixel, 6 with satgrow > 0, plus 512 KiB and 3
- * bytes per 32x64 tile per frame, and 1.5 MiB for a frame whose gain is
+ * bytes per 32x32 tile per frame, and 1.5 MiB for a frame whose gain is
  * estimated; lacos_request_bytes gives the figure), charged against the
  * context's HBM budget.
  *
@@ -233,14 +233,15 @@ int lacos_run_static(const void *d_frame, lacos_dtype dt, int ny, int nx, const 
  *   0..3: 32 x 64 tiles, 256 threads, 1..4 CTAs per SM (more CTAs hide more
  *         latency, fewer registers spill more; 3 is the default);
  *   4, 5: 64 x 64 tiles, 512 threads, 1 or 2 CTAs per SM;
- *   6, 7: 32 x 128 tiles, 512 threads, 1 or 2 CTAs per SM.
+ *   6, 7: 32 x 128 tiles, 512 threads, 1 or 2 CTAs per SM;
+ *   8, 9: 32 x 32 tiles, 160 threads, 5 or 6 CTAs per SM.
  * Larger tiles recompute less of the halo (each tile evaluates its medians
  * up to 6 pixels beyond its edges) but hold more shared memory per CTA.
  * lacos_autotune runs the given frame `reps` times (after one warm-up) with
  * each variant, keeps the fastest, and reports each variant's mean device
  * time in variant_ms[LACOS_CORE_VARIANTS] (may be NULL).  Results do not
  * depend on the variant. */
-#define LACOS_CORE_VARIANTS 8
+#define LACOS_CORE_VARIANTS 10
 int lacos_set_core_variant(lacos_ctx *c, int variant);
 int lacos_get_core_variant(lacos_ctx *c, int *variant);
 int lacos_autotune(lacos_ctx *c, const void *d_frame, lacos_dtype dt, int ny, int nx,

@@ -106,9 +106,9 @@ bool same_batch(const std::vector<FrameReq>& a, const std::vector<FrameReq>& b) 
 int wpr_of(int nx) { return (nx + 31) / 32; }
 size_t maskbuf_bytes(int ny, int nx) { return align_up((size_t)ny * wpr_of(nx) * sizeof(uint32_t)); }
 // Per-tile level marks of the core kernel: two ping-pong bytes and a sticky one per
-// tile, sized for the smallest core tile (32 x 64) so that every variant fits.
+// tile, sized for the smallest core tile (32 x 32) so that every variant fits.
 size_t tflag_bytes(int ny, int nx) {
-  return align_up(3 * (size_t)((nx + G32x64::TW - 1) / G32x64::TW) * (size_t)((ny + G32x64::TH - 1) / G32x64::TH));
+  return align_up(3 * (size_t)((nx + G32x32::TW - 1) / G32x32::TW) * (size_t)((ny + G32x32::TH - 1) / G32x32::TH));
 }
 
 struct Layout {
@@ -154,7 +154,8 @@ constexpr CoreVariant make_variant() {
 }
 static const CoreVariant kCoreVariants[LACOS_CORE_VARIANTS] = {
     make_variant<G32x64, 1>(), make_variant<G32x64, 2>(), make_variant<G32x64, 3>(), make_variant<G32x64, 4>(),
-    make_variant<G64x64, 1>(), make_variant<G64x64, 2>(), make_variant<G32x128, 1>(), make_variant<G32x128, 2>()};
+    make_variant<G64x64, 1>(), make_variant<G64x64, 2>(), make_variant<G32x128, 1>(), make_variant<G32x128, 2>(),
+    make_variant<G32x32, 5>(), make_variant<G32x32, 6>()};
 constexpr int kDefaultCoreVariant = 3;
 
 struct lacos_ctx {

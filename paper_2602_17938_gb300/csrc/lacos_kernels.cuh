@@ -96,12 +96,13 @@ struct Geo {
   };
   using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
   using XR3 = Reg<3, 8>;  // finalize
-  static_assert(TW % 64 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
+  static_assert(TW % 32 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
 };
 // The variants' tile shapes.  Finalize always runs on 32 x 64 tiles.
 using G32x64 = Geo<32, 64, 256>;
 using G64x64 = Geo<64, 64, 512>;
 using G32x128 = Geo<32, 128, 512>;
+using G32x32 = Geo<32, 32, 160>;
 using FG = G32x64;
 
 constexpr unsigned ERR_NONFINITE = 1u;
@@ -870,7 +871,9 @@ constexpr bool core_layout_ok() {
          offsetof(U, S) % 8 == 0 && offsetof(U, flags) % 8 == 0 && offsetof(F, N) % 8 == 0 &&
          offsetof(U, DY) % 16 == 0 && G::TH * G::TW <= G::template Reg<4>::N && G::XR6::N <= 65536;
 }
-static_assert(core_layout_ok<G32x64>() && core_layout_ok<G64x64>() && core_layout_ok<G32x128>(), "core layout");
+static_assert(core_layout_ok<G32x64>() && core_layout_ok<G64x64>() && core_layout_ok<G32x128>() &&
+                  core_layout_ok<G32x32>(),
+              "core layout");
 // Dynamic shared memory of a core launch, by geometry and working-image type.
 template <class G, class XT>
 constexpr size_t kCoreSmemBytes = sizeof(CoreSmemT<G, XT>);

@@ -20,7 +20,7 @@ LACOS_F32, LACOS_U16 = 0, 1
 OK, PENDING = 0, 1
 EINVAL, EAGAIN, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNKNOWN_TICKET, ENOGAIN = -1, -2, -3, -4, -5, -6, -7, -8
 MAX_NITER = 256
-CORE_VARIANTS = 8  # LACOS_CORE_VARIANTS: core-kernel tile shape x occupancy variants
+CORE_VARIANTS = 10  # LACOS_CORE_VARIANTS: core-kernel tile shape x occupancy variants
 _ERRNAMES = {EINVAL: "EINVAL", EAGAIN: "EAGAIN", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
              ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT", EUNKNOWN_TICKET: "EUNKNOWN_TICKET",
              ENOGAIN: "ENOGAIN"}

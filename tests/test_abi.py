@@ -40,8 +40,8 @@ def test_host_only_entry_points(lib):
     n = lib.lacos_scratch_bytes(6388, 9576)
     # five bit-planes (two mask buffers, three test planes): 5 * 6388 * ceil(9576/32) * 4,
     # the 65536-entry table of {2N, 1/(2N)} (float pairs) per uint16 med5 value, and three
-    # level-mark bytes per 32x64 core tile: 3 * ceil(6388/32) * ceil(9576/64)
-    expect = 5 * 6388 * 300 * 4 + 65536 * 8 + 3 * 200 * 150
+    # level-mark bytes per tile of the smallest core tile, 32x32: 3 * ceil(6388/32) * ceil(9576/32)
+    expect = 5 * 6388 * 300 * 4 + 65536 * 8 + 3 * 200 * 300
     assert expect <= n < expect + (1 << 20)
     assert lib.lacos_scratch_bytes(0, 5) == 0
 

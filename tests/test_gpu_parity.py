@@ -368,7 +368,7 @@ def test_core_variants_on_the_batched_path(ctx):
     ps = [lacos.make_params(g, rn, **kw) for _, g, rn, kw in cases]
     v0 = ctx.core_variant()
     try:
-        for v in (3, 5, 7):
+        for v in (3, 5, 7, 9):
             ctx.set_core_variant(v)
             masks = [torch.empty(f.shape, dtype=torch.uint8, device="cuda") for f in d]
             cleans = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in d]
