@@ -142,3 +142,28 @@ def test_static_entry_point_estimates_the_gain(lib):
     r = lib.run_static(d, lib.make_params(0.0, 5.0, niter=4), m, c)
     torch.cuda.synchronize()
     _assert_same(m.cpu().numpy(), c.cpu().numpy(), r, oracle.run(frame, 0.0, 5.0, niter=4, return_gain=True))
+
+
+def test_histogram_bin_sums_wrap_and_extreme_differences(lib):
+    # A bright, nearly flat uint16 frame (65500 ADU, 8% of pixels one higher) of 7200 x 7200
+    # with the saturation guard off: on 152 SMs each histogram block sees about 36000 pairs
+    # with d = 0, so that bin's sum of a + b (131000 per pair) passes 2^32 within one block
+    # and the 32-bit shared sum must carry.  A few pairs (0, 65535) and (65535, 0) put
+    # d = -65535 and +65535 in the outermost bins (clipped in the first round).  The level-1
+    # gain must equal the oracle's estimate on the same image (reading C15), bit for bit
+    # after rounding to float.
+    ny = nx = 7200
+    rng = np.random.default_rng(7200)
+    f = np.full((ny, nx), 65500, np.int32) + (rng.random((ny, nx)) < 0.08)
+    for y in range(100, 7100, 700):
+        f[y, 100:104] = (0, 65535, 65535, 0)  # pairs (0, 65535) and (65535, 0) at even columns
+    frame = f.astype(np.uint16)
+    z = np.zeros(frame.shape, np.uint8)
+    g_ref, rounds, stats = oracle.estimate_gain(frame.astype(np.float32), z, z, 2.0)
+    assert g_ref is not None and rounds >= 1
+    p = lib.make_params(0.0, 2.0, satlevel=0.0, niter=1)
+    m, c, r = _device_run(lib, frame, p)
+    assert r.status == 0 and r.iters_run == 1
+    assert r.gain == np.float32(g_ref)
+    keep = m == 0
+    assert np.array_equal(c[keep], frame[keep].astype(np.float32))
