@@ -33,7 +33,7 @@ WORKLOAD = "lacosmic_9576x6388_u16_niter4"
 # DRAM bytes (read + write) per core_kernel launch from one ncu capture on
 # this workload, keyed by kernel_source_sha() of the captured build; any other
 # source reports null (the counters no longer describe the kernel).
-NCU_CORE_TRAFFIC = {"6a0257744c9513d9": 131_703_552 + 17_389_824}
+NCU_CORE_TRAFFIC = {"b102efec156638f1": 131_779_840 + 17_377_280}
 
 
 def kernel_source_sha() -> str:
@@ -415,8 +415,10 @@ def run_serving(args, dev):
     points = []
     plan = SERVING_POINTS_FULL if args.serving_full else SERVING_POINTS
     with serve.Server(dev.index or 0, hbm_budget_bytes=120 << 30, max_slots=96) as srv:
-        # Warm-up: every slot the sweep can use gets its stream and scratch.
+        # Warm-up: every slot the sweep can use gets its stream and scratch, and
+        # the server its output buffers of both frame sizes.
         srv.run([serve.Request(pool_big[i % len(pool_big)], p, 0.0) for i in range(96)])
+        srv.run([serve.Request(pool_small[i % len(pool_small)], p, 0.0) for i in range(24)])
         for rate, n in plan:
             arr = synth.poisson_arrivals(rate, n) if math.isfinite(rate) else [0.0] * n
             reqs, nb, ns = [], 0, 0
@@ -431,7 +433,14 @@ def run_serving(args, dev):
                            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                            "max_ms": max(r.latency for r in st.records) * 1e3,
                            "mpix_per_s": st.mpix_per_s, "max_in_flight": st.max_in_flight,
-                           "makespan_s": st.makespan_s})
+                           "makespan_s": st.makespan_s,
+                           # where the slowest requests lost their time: waiting for
+                           # admission, or between submission and completion
+                           "slowest": [{"arrival_s": round(r.arrival, 4),
+                                        "wait_ms": round((r.admitted - r.arrival) * 1e3, 3),
+                                        "run_ms": round((r.done - r.admitted) * 1e3, 3),
+                                        "mpx": round(r.npix / 1e6, 2)}
+                                       for r in sorted(st.records, key=lambda r: -r.latency)[:6]]})
     del pool_big, pool_small
     torch.cuda.empty_cache()
     return {"workload": "Poisson arrivals of 9576x6388 u16 frames, 10% 2048x2048 f32 (seed 3); "

@@ -88,7 +88,22 @@ class Server:
                 torch.empty((ny, nx), dtype=torch.float32, device=self.device))
 
     def run(self, requests: list, poll_sleep: float = 2e-5) -> Stats:
-        """Serve the requests (sorted by arrival) and return latency/throughput stats."""
+        """Serve the requests (sorted by arrival) and return latency/throughput stats.
+
+        The cyclic garbage collector is held off while the loop runs (a full
+        collection of a large heap would stall admission and polling for
+        milliseconds); it is restored, and run once, afterwards."""
+        import gc
+        enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, poll_sleep)
+        finally:
+            if enabled:
+                gc.enable()
+                gc.collect()
+
+    def _run(self, requests, poll_sleep):
         import torch
         torch.cuda.synchronize(self.device)
         order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
