@@ -33,7 +33,7 @@ WORKLOAD = "lacosmic_9576x6388_u16_niter4"
 # DRAM bytes (read + write) per core_kernel launch from one ncu capture on
 # this workload, keyed by kernel_source_sha() of the captured build; any other
 # source reports null (the counters no longer describe the kernel).
-NCU_CORE_TRAFFIC = {"b102efec156638f1": 131_779_840 + 17_377_280}
+NCU_CORE_TRAFFIC = {"3db5e50f8c301cfc": 132_058_624 + 17_459_712}
 
 
 def kernel_source_sha() -> str:
