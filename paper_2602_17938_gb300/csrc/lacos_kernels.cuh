@@ -98,14 +98,17 @@ struct Geo {
   using XR3 = Reg<3, 8>;  // finalize
   static_assert(TW % 32 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
 };
-// The core variants' tile shapes.  Finalize runs on 32 x 128 tiles with
-// 256 threads: twice the pixels of a 32 x 64 tile per staging and per
-// barrier (18% less time per frame than 32 x 64), still six CTAs per SM.
+// The core variants' tile shapes.
 using G32x64 = Geo<32, 64, 256>;
 using G64x64 = Geo<64, 64, 512>;
 using G32x128 = Geo<32, 128, 512>;
 using G32x32 = Geo<32, 32, 160>;
-using FG = Geo<32, 128, 256>;
+// Finalize tiles, 256 threads: 32 x 128 for requests of many tiles (twice
+// the pixels of a 32 x 64 tile per staging and per barrier: 18% less time
+// on a 61-Mpx frame), 32 x 64 for small requests, which the larger tiles
+// would leave with too few blocks.
+using FGBig = Geo<32, 128, 256>;
+using FGSmall = Geo<32, 64, 256>;
 
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -162,7 +165,7 @@ struct FrameDesc {
   int th, tw;        // core tile shape of the request's core-kernel variant
   int tiles_x;       // core tiles per row
   unsigned int tile_begin, tile_end;    // this frame's range in the flattened core-tile list
-  int ftiles_x;                         // finalize tiles (32 x 128) per row
+  int ftiles_x;                         // finalize tiles per row
   unsigned int fin_begin, fin_end;      // this frame's range in the flattened finalize-tile list
   unsigned long long word_begin;        // this frame's range in the flattened word list
   unsigned int gblk_begin, gblk_x;      // growth items: this frame's first, column groups per strip
@@ -1505,11 +1508,16 @@ __device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
   return c | (c << 1) | (c >> 1) | (l >> 31) | (r << 31);
 }
 
-// Growth block: 64 rows x 16 words, four words per thread (12% less time per
-// level than 32 x 8 blocks: the halo words are a smaller share).
-constexpr int GB_H = 64, GB_W = 16;
-constexpr int GB_WPT = GB_H * GB_W / kBlock;  // words per thread
-static_assert(GB_H * GB_W == GB_WPT * kBlock, "whole words per thread");
+// Growth blocks of H rows x W words, WPT words per thread: 64 x 16 for
+// requests of many blocks (12% less time per level on a 61-Mpx frame than
+// 32 x 8: the halo words are a smaller share), 32 x 8 for small requests.
+template <int H_, int W_>
+struct GrowGeo {
+  static constexpr int H = H_, W = W_, WPT = H * W / kBlock;
+  static_assert(H * W == WPT * kBlock, "whole words per thread");
+};
+using GrowBig = GrowGeo<64, 16>;
+using GrowSmall = GrowGeo<32, 8>;
 
 __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, unsigned b) {
   int lo = 0, hi = nframes - 1;
@@ -1520,15 +1528,16 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
   return lo;
 }
 
-// Step 6 for a block of GB_H rows x GB_W words: the candidate words (with a
+// Step 6 for a block of GG::H rows x GG::W words: the candidate words (with a
 // 2-row, 2-word halo) and the first growth g1 = dil3(cand) & sig (1-row,
 // 1-word halo) are staged in shared memory; each thread then forms
 // g2 = dil3(g1) & lo for its words, M_k = M_{k-1} | g2, and counts new flags.
 // Every global load of the block (candidate, sig, lo and mask words) is
 // issued up front, so the block waits for one memory round trip.
+template <class GG>
 __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                       unsigned total_blocks, int k) {
-  constexpr int NT = kBlock;
+  constexpr int NT = kBlock, GB_H = GG::H, GB_W = GG::W, GB_WPT = GG::WPT;
   constexpr int CW = GB_W + 4, CN = (GB_H + 4) * CW;  // candidate region
   constexpr int GW = GB_W + 2, GN = (GB_H + 2) * GW;  // g1 region
   constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
@@ -1605,7 +1614,7 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
 
 // ---- output: cleaned frame and uint8 mask of the last mask ----------------
 
-template <class XT>
+template <class FG, class XT>
 struct FinalSmemT {
   XT X[FG::XR3::N];
   uint8_t Mb[FG::XR3::N];
@@ -1613,14 +1622,13 @@ struct FinalSmemT {
   uint16_t list[FG::TH * FG::TW];
   unsigned nlist;
 };
-constexpr size_t kFinalSmemBytes = sizeof(FinalSmemT<float>);
 
 // The rare replacements whose 5x5 window is fully flagged: the 7x7 window
 // from shared memory, else wider windows from global memory.  Kept out of
 // line so that the common path's register allocation does not carry the
 // 49-key network.
-template <class XT>
-__device__ __noinline__ XT replace_wide(const FrameDesc& f, const uint32_t* M, const FinalSmemT<XT>& sm, int c,
+template <class FG, class XT>
+__device__ __noinline__ XT replace_wide(const FrameDesc& f, const uint32_t* M, const FinalSmemT<FG, XT>& sm, int c,
                                         int gy, int gx) {
   XT v;
   if (!maskmed7(sm.X, sm.Mb, FG::XR3::W, c, v)) v = (XT)maskmed_wide(f, M, gy, gx, 4);
@@ -1632,10 +1640,10 @@ __device__ __noinline__ XT replace_wide(const FrameDesc& f, const uint32_t* M, c
 // flagged pixels of a tile are compacted into a list, replaced in shared
 // memory, and the tile is then written out coalesced, four pixels per
 // thread where the row pitch allows 16-byte stores.
-template <class XT>
-__device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& sm) {
+template <class FG, class XT>
+__device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<FG, XT>& sm) {
   constexpr int TH = FG::TH, TW = FG::TW, TWW = FG::TWW, NT = kBlock;
-  using XR3 = FG::XR3;
+  using XR3 = typename FG::XR3;
   static_assert(FG::NT == kBlock, "finalize geometry");
   const int tid = threadIdx.x;
   const int oy = (tix / f.ftiles_x) * TH, ox = (tix % f.ftiles_x) * TW;
@@ -1663,7 +1671,7 @@ __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& s
     const int ly = i / TW, lx = i % TW;
     const int c = XR3::idx(ly, lx);
     XT v;
-    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v)) v = replace_wide(f, M, sm, c, oy + ly, ox + lx);
+    if (!maskmed5(sm.X, sm.Mb, XR3::W, c, v)) v = replace_wide<FG, XT>(f, M, sm, c, oy + ly, ox + lx);
     sm.X[c] = v;
   }
   __syncthreads();
@@ -1695,9 +1703,10 @@ __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<XT>& s
   return n;
 }
 
+template <class FG>
 __global__ void __launch_bounds__(kBlock, 6) finalize_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                          unsigned total, unsigned* head) {
-  __shared__ __align__(16) unsigned char smem[kFinalSmemBytes];
+  __shared__ __align__(16) unsigned char smem[sizeof(FinalSmemT<FG, float>)];
   __shared__ unsigned s_item;
   const int tid = threadIdx.x;
   __shared__ unsigned long long flagged;  // flagged pixels of frame acc_st so far (thread 0)
@@ -1715,15 +1724,15 @@ __global__ void __launch_bounds__(kBlock, 6) finalize_kernel(const FrameDesc* __
     const int tix = (int)(item - f.fin_begin);
     unsigned n;
     if (f.dtype == 1) {
-      auto& sm = *reinterpret_cast<FinalSmemT<uint16_t>*>(smem);
+      auto& sm = *reinterpret_cast<FinalSmemT<FG, uint16_t>*>(smem);
       if (tid == 0) sm.nlist = 0;
       __syncthreads();
-      n = finalize_tile<uint16_t>(f, tix, sm);
+      n = finalize_tile<FG, uint16_t>(f, tix, sm);
     } else {
-      auto& sm = *reinterpret_cast<FinalSmemT<float>*>(smem);
+      auto& sm = *reinterpret_cast<FinalSmemT<FG, float>*>(smem);
       if (tid == 0) sm.nlist = 0;
       __syncthreads();
-      n = finalize_tile<float>(f, tix, sm);
+      n = finalize_tile<FG, float>(f, tix, sm);
     }
     if (tid == 0) {
       if (f.st != acc_st) {
