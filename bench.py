@@ -33,7 +33,7 @@ WORKLOAD = "lacosmic_9576x6388_u16_niter4"
 # DRAM bytes (read + write) per core_kernel launch from one ncu capture on
 # this workload, keyed by kernel_source_sha() of the captured build; any other
 # source reports null (the counters no longer describe the kernel).
-NCU_CORE_TRAFFIC = {"3db5e50f8c301cfc": 132_058_624 + 17_459_712}
+NCU_CORE_TRAFFIC = {"82f726a5357a5ade": 131_695_104 + 17_459_712}
 
 
 def kernel_source_sha() -> str:
@@ -569,6 +569,7 @@ def run_ours(args):
     peak = min(peak_f32, peak_u16) / 1e3 if (peak_f32 and peak_u16) else None
     share = per_kernel["core"] / sum(per_kernel.values())
     by_kind = {k: sum(w[k] for w in works) / len(works) for k in ("dense_instr", "sprime_instr", "fine_instr")}
+    as_networks = sum(w["instr_as_networks"] for w in works) / len(works)
     # End to end through the public API: lacos_submit_host copies the pinned
     # host frame in and the mask and cleaned frame out inside every step;
     # E2E_DEPTH requests in flight overlap one step's upload, another's
@@ -638,9 +639,17 @@ def run_ours(args):
                      "peak_source": "measured: min/max issue rate of the ALU pipe (csrc/alu_peak.cu), "
                                     "the lower of its f32 and u16x2 figures",
                      "work": "per step: dense med5+med3 networks at computed tile pixels (packed u16x2, "
-                             "half an instruction per output-op) + med5 at S' items + med7 at F items",
+                             "half an instruction per output-op) + at S' items the med5 network (fine items) "
+                             "or the lo test by rank (25 compares) + at F items the objlim test by rank "
+                             "(49 compares; the med7 network where the rank search does not settle)",
                      "work_instr_per_step": by_kind,
                      "ideal_ms_per_step": (sum(by_kind.values()) / (peak * 1e12) * 1e3) if peak else None,
+                     "medians_as_networks": {
+                         "instr_per_step": as_networks,
+                         "frac": (as_networks / (peak * 1e12) / (per_kernel["core"] / len(profs) * 1e-3))
+                         if peak else None,
+                         "note": "the same medians costed as if each ran its selection network (the work "
+                                 "counted before the sparse tests were decided by rank)"},
                      "avg_launch_ms": det_avg_ms, "launch_share": share,
                      "kernel_ms_per_step": {k: v / len(profs) for k, v in per_kernel.items()}},
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": 2 * npix,
@@ -651,7 +660,8 @@ def run_ours(args):
         "wall_s_timed": t_wall,
         "check_clean_equals_input_outside_mask": ok_check,
         "alu_peak_gops": {"f32": peak_f32, "u16x2": peak_u16},
-        "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_fine", "n_replace", "n_replace_wide")},
+        "sparse_work_per_step": {k: profs[-1][k] for k in ("n_sprime", "n_sprime_net", "n_fine", "n_fine_net",
+                                                            "n_replace", "n_replace_wide")},
         "modes": modes,
     }
     line["core_variant"] = {"chosen": variant, "ms_per_variant": variant_ms}

@@ -196,6 +196,10 @@ typedef struct {
   long long n_replace_wide;            /* ... of which the 5x5 window was fully flagged */
   long long px_core;                   /* tile pixels the core kernel computed, all levels (a
                                           level recomputes only tiles whose inputs changed) */
+  long long n_sprime_net;              /* ... of n_sprime, those that ran the med5 network (the
+                                          others needed only the lo test, decided by rank) */
+  long long n_fine_net;                /* ... of n_fine, those that ran the med7 network (float32
+                                          frames; uint16 frames decide the objlim test by rank) */
 } lacos_profile;
 
 int lacos_set_profiling(lacos_ctx *c, int on);

@@ -584,6 +584,8 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
       P.n_replace += (long long)hs[i].n_replace;
       P.n_replace_wide += (long long)hs[i].n_replace_wide;
       P.px_core += (long long)hs[i].px_core;
+      P.n_sprime_net += (long long)hs[i].n_sprime_net;
+      P.n_fine_net += (long long)hs[i].n_fine_net;
     }
   }
   for (int i = 0; i < sl.nframes; ++i) {
@@ -606,7 +608,7 @@ static int finish(lacos_ctx* c, Slot& sl, lacos_result* res) {
 
 extern "C" {
 
-const char* lacos_version(void) { return "lacos-gb300 0.3 (sm_103a)"; }
+const char* lacos_version(void) { return "lacos-gb300 0.4 (sm_103a)"; }
 
 int lacos_selftest_division(float gain, float readnoise, unsigned long long* mismatches) {
   if (!mismatches || !(gain > 0.0f) || !(readnoise >= 0.0f) || !std::isfinite(gain) || !std::isfinite(readnoise))

@@ -126,6 +126,7 @@ struct FrameState {
   unsigned long long n_sprime, n_fine, n_replace;  // sparse-work counters (profiling)
   unsigned long long n_replace_wide;               // replacements whose 5x5 window was all flagged
   unsigned long long px_core;                      // tile pixels the core kernel computed (all levels)
+  unsigned long long n_sprime_net, n_fine_net;     // S' and F evaluations by the full median networks
   unsigned int err;
   int iters_run;
   // Gain estimation (frames with gain 0), per level: the range of d present
@@ -846,7 +847,7 @@ template <class G> struct CoreSmemT<G, float> {
   uint32_t pw[3][G::TH][G::TWW];         // the tile's sig, lo and candidate bit-plane words
   uint32_t Sw[G::TH][G::TWW];            // satgrow > 0: the tile's words of the grown saturated set
   unsigned nlist, nlist2;                // list lengths (S'-only, fine-structure)
-  unsigned nfine;                        // F evaluations of the tile
+  unsigned nfine, nfine_net;             // F evaluations of the tile; of them by the med7 network
 };
 template <class G> struct CoreSmemT<G, uint16_t> {
   using XR6 = typename G::XR6;
@@ -861,7 +862,7 @@ template <class G> struct CoreSmemT<G, uint16_t> {
   uint32_t pw[3][G::TH][G::TWW];
   uint32_t Sw[G::TH][G::TWW];
   unsigned nlist, nlist2;
-  unsigned nfine;
+  unsigned nfine, nfine_net;
 };
 // Alignment of the vector accesses: 16-byte staging rows (X; Mb in 8-byte
 // groups), 4-pixel block-network loads, 2-pixel pairs of S, N, DY and flags;
@@ -1211,11 +1212,81 @@ __device__ __forceinline__ void dense_pixels(const FrameDesc& f, CoreSmemT<G, XT
   warp_emit(hits, &sm.nlist, sm.list, R4::N - 1, tix);
 }
 
+// The objlim test of step 5 at a pixel with S' = sp, noise N and med3 - med7
+// difference diff: F = max(diff / N, 0.01) (diff itself without the
+// normalisation), then S' / F > objlim.
+// (diff <= 0 gives F = 0.01 whether or not it is divided by N > 0.)
+__device__ __forceinline__ bool objlim_test(const FrameDesc& f, float sp, float N, float diff) {
+  float F = 0.01f;
+  if (diff > 0.0f) {
+    F = f.fnorm ? __fdiv_rn(diff, N) : diff;
+    F = F < 0.01f ? 0.01f : F;
+  }
+  return __fdiv_rn(sp, F) > f.objlim;
+}
+
+// The lo test of an S'-only item, fl(S - med5(S)) > lo, without the median.
+// fl(S - x) can only fall as x grows, so the values x that pass form a lower
+// set, and the median (rank 12 of the 25 window values, counted with
+// multiplicity) passes iff at least 13 of the 25 values pass.
+template <class LD>
+__device__ __forceinline__ bool rank_lo_test(float Sc, float lo, const LD& ld5) {
+  int pass = 0;
+#pragma unroll
+  for (int e = 0; e < 25; ++e) pass += __fsub_rn(Sc, ld5(e)) > lo;
+  return pass >= 13;
+}
+
+// The objlim test of a uint16 frame without the med7 network.  The med3
+// values are integers below 2^16, so the float difference m3 - v is exact
+// and F depends on d = m3 - v alone; with S' > 0 the test can only turn from
+// true to false as d grows (F is non-decreasing in d, S'/F non-increasing in
+// F).  So the values v that pass are those v >= m3 - d*, d* the largest d
+// that passes, and the median (rank 24 of the 49 window values) passes iff
+// at least 25 of them do.  d* is taken from the real-number threshold
+// (S'/objlim, times N when F is normalised) and confirmed with the float
+// test itself at d* and d* + 1; the search moves at most four steps, and
+// returns -1 when it has not settled (the caller then runs the network).
+template <int W3>
+__device__ __forceinline__ int objlim_rank_u16(const FrameDesc& f, float sp, float N, int m3, const uint16_t* w7) {
+  if (!(sp > 0.0f)) return -1;
+  const int dlo = m3 - 65535, dhi = m3;  // d over every possible med7 value 65535 .. 0
+  const auto pass = [&](int d) { return objlim_test(f, sp, N, (float)d); };
+  int ds;
+  if (!pass(dlo)) {
+    ds = dlo - 1;  // no med7 value passes
+  } else if (pass(dhi)) {
+    ds = dhi;  // every med7 value passes
+  } else {     // pass(dlo) and not pass(dhi): dlo <= d* < dhi
+    const float x = f.fnorm ? __fmul_rn(__fdiv_rn(sp, f.objlim), N) : __fdiv_rn(sp, f.objlim);
+    int d = !(x > (float)dlo) ? dlo : (x > (float)dhi ? dhi - 1 : (int)ceilf(x) - 1);
+    d = clampi(d, dlo, dhi - 1);
+    ds = dlo - 2;  // unsettled
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      if (!pass(d)) {  // then d > dlo
+        --d;
+      } else if (pass(d + 1)) {  // then d + 1 < dhi
+        ++d;
+      } else {
+        ds = d;
+        break;
+      }
+    }
+    if (ds == dlo - 2) return -1;
+  }
+  const int t = m3 - ds;  // v passes iff v >= t
+  int n = 0;
+#pragma unroll
+  for (int e = 0; e < 49; ++e) n += (int)w7[(e / 7) * W3 + e % 7] >= t;
+  return n >= 25 ? 1 : 0;
+}
+
 // Work counters of a tile (valid in thread 0).  A block sums them over its
 // tiles and adds them to the frame's state once per frame it leaves, instead
 // of one same-address atomic per tile.
 struct TileCounts {
-  unsigned long long px = 0, sprime = 0, fine = 0, replace = 0;
+  unsigned long long px = 0, sprime = 0, fine = 0, replace = 0, sprime_net = 0, fine_net = 0;
 };
 
 __device__ __forceinline__ void flush_counts(FrameState* st, const TileCounts& c) {
@@ -1224,6 +1295,8 @@ __device__ __forceinline__ void flush_counts(FrameState* st, const TileCounts& c
   if (c.sprime) atomicAdd(&st->n_sprime, c.sprime);
   if (c.fine) atomicAdd(&st->n_fine, c.fine);
   if (c.replace) atomicAdd(&st->n_replace, c.replace);
+  if (c.sprime_net) atomicAdd(&st->n_sprime_net, c.sprime_net);
+  if (c.fine_net) atomicAdd(&st->n_fine_net, c.fine_net);
 }
 
 template <class G, class XT>
@@ -1245,7 +1318,7 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<G,
   TileCounts counts;
 
   for (int i = tid; i < 3 * TH * TWW; i += NT) (&sm.pw[0][0][0])[i] = 0u;
-  if (tid == 0) sm.nfine = 0;
+  if (tid == 0) sm.nfine = sm.nfine_net = 0;
 
   // The tile's words of the grown saturated set (satgrow > 0): the load is
   // issued before the staging and stored after it, so it waits for nothing.
@@ -1348,9 +1421,12 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<G,
   // med7(med3))/N, 0.01) and the objlim test S'/F > objlim.  Fine items (the
   // costly ones) come first and rounds alternate direction, so the cheap
   // S'-only items of a second round land on the threads without a fine item.
+  // An S'-only item needs nothing but the lo test, which is decided by rank
+  // (rank_lo_test); the objlim test of a uint16 frame is decided by rank too
+  // (objlim_rank_u16).  Both give the bit the median would give.
   if (edge) __syncthreads();
   const unsigned n = sm.nlist, n2 = sm.nlist2, total = n + n2;
-  unsigned n_eval = 0;
+  unsigned n_eval = 0, n_net7 = 0;
   for (unsigned r = 0; r * NT < total; ++r) {
     const unsigned q = r * NT + ((r & 1) ? (NT - 1 - tid) : tid);
     if (q >= total) continue;
@@ -1360,35 +1436,52 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<G,
     const int c = R2::idx(ly, lx);
     const float* wb = sm.S + c - 2 * R2::W - 2;
     const auto ld5 = [&](int e) { return wb[(e / 5) * R2::W + e % 5]; };
+    const bool sat = (sm.flags[i] & 8) != 0;  // never set for fine items
+    const uint32_t bit = 1u << (lx & 31);
+    if (!fine && !f.sepmed) {  // S'-only item: S' <= S <= sigclip, or saturated
+      if (!sat && rank_lo_test(sm.S[c], f.lo, ld5)) atomicOr(&sm.pw[1][ly][lx >> 5], bit);
+      continue;
+    }
     float m;
     if (f.sepmed)
       sep5x5_ld<float>(ld5, &m);
     else
       med5x5_ld<float>(ld5, &m);
     const float sp = __fsub_rn(sm.S[c], m);
-    const bool sat = (sm.flags[i] & 8) != 0;  // never set for fine items
-    const uint32_t bit = 1u << (lx & 31);
     if (!sat && sp > f.lo) atomicOr(&sm.pw[1][ly][lx >> 5], bit);
     if (!fine || !(sp > f.sigclip)) continue;  // S'-only items have S' <= S <= sigclip
     atomicOr(&sm.pw[0][ly][lx >> 5], bit);
+    ++n_eval;
     const int c3 = R3::idx(ly, lx);
     const XT* w7 = sm.M3 + c3 - 3 * R3::W - 3;
-    const auto ld7 = [&](int e) { return KT::key(w7[(e / 7) * R3::W + e % 7]); };
-    K m7;
-    med7x7_ld<K>(ld7, &m7);
-    ++n_eval;
-    const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
     float N;
     if constexpr (kU16)
       N = __fmul_rn(sm.DY[c].x, 0.5f);  // the table holds 2N; halving is exact
     else
       N = sm.N[i];
-    float F = f.fnorm ? __fdiv_rn(diff, N) : diff;
-    F = F < 0.01f ? 0.01f : F;
-    if (__fdiv_rn(sp, F) > f.objlim) atomicOr(&sm.pw[2][ly][lx >> 5], bit);
+    int cand = -1;
+    if constexpr (kU16) cand = objlim_rank_u16<R3::W>(f, sp, N, (int)sm.M3[c3], w7);
+    if (cand < 0) {  // float frames, and searches that did not settle: the med7 network
+      const auto ld7 = [&](int e) { return KT::key(w7[(e / 7) * R3::W + e % 7]); };
+      K m7;
+      med7x7_ld<K>(ld7, &m7);
+      ++n_net7;
+      const float diff = __fsub_rn((float)sm.M3[c3], (float)KT::back(m7));
+      cand = objlim_test(f, sp, N, diff);
+    }
+    if (cand) atomicOr(&sm.pw[2][ly][lx >> 5], bit);
   }
   n_eval = __reduce_add_sync(0xffffffffu, n_eval);
   if ((tid & 31) == 0 && n_eval) atomicAdd(&sm.nfine, n_eval);
+  if constexpr (!kU16) {
+    n_net7 = __reduce_add_sync(0xffffffffu, n_net7);
+    if ((tid & 31) == 0 && n_net7) atomicAdd(&sm.nfine_net, n_net7);
+  } else {
+    if (__any_sync(0xffffffffu, n_net7 != 0)) {  // rare: only searches that did not settle
+      n_net7 = __reduce_add_sync(0xffffffffu, n_net7);
+      if ((tid & 31) == 0) atomicAdd(&sm.nfine_net, n_net7);
+    }
+  }
   __syncthreads();
 
   // Bit-planes of the tile out (only in-frame pixels ever set a bit).
@@ -1404,6 +1497,8 @@ __device__ TileCounts core_tile(const FrameDesc& f, int k, int tix, CoreSmemT<G,
     counts.px = (unsigned long long)(min(TH, ny - oy) * min(TW, nx - ox));
     counts.sprime = total;
     counts.fine = sm.nfine;
+    counts.sprime_net = f.sepmed ? total : n2;
+    counts.fine_net = sm.nfine_net;
   }
   return counts;
 }
@@ -1464,6 +1559,8 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
       acc.sprime += c.sprime;
       acc.fine += c.fine;
       acc.replace += c.replace;
+      acc.sprime_net += c.sprime_net;
+      acc.fine_net += c.fine_net;
     }
     __syncthreads();
   }

@@ -47,7 +47,8 @@ class Profile(ctypes.Structure):
                 ("final_ms", ctypes.c_float), ("px_iterations", ctypes.c_longlong),
                 ("n_sprime", ctypes.c_longlong), ("n_fine", ctypes.c_longlong),
                 ("n_replace", ctypes.c_longlong), ("n_replace_wide", ctypes.c_longlong),
-                ("px_core", ctypes.c_longlong)]
+                ("px_core", ctypes.c_longlong), ("n_sprime_net", ctypes.c_longlong),
+                ("n_fine_net", ctypes.c_longlong)]
 
 
 class Result(ctypes.Structure):
@@ -263,7 +264,7 @@ class Context:
                 "final_ms": p.final_ms,
                 "px_iterations": p.px_iterations, "n_sprime": p.n_sprime, "n_fine": p.n_fine,
                 "n_replace": p.n_replace, "n_replace_wide": p.n_replace_wide,
-                "px_core": p.px_core}
+                "px_core": p.px_core, "n_sprime_net": p.n_sprime_net, "n_fine_net": p.n_fine_net}
 
     def last_cuda_error(self) -> int:
         return self.lib.lacos_last_cuda_error(self.h)

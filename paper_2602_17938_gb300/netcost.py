@@ -1,18 +1,26 @@
-"""Static min/max operation counts of the selection networks the kernels run.
+"""Static operation counts of the selection networks and rank tests the kernels run.
 
 The core kernel's "algorithmic" work, used for its ALU roofline, is the
 number of two-input min/max operations its median networks perform per
 output pixel and iteration -- the shared-block med5 (for N) and med3
-networks, per output -- plus the data-dependent S' = S - med5(S) at the
-pixels where S exceeds the lower threshold (standalone med5 network).
-Halo recomputation is not counted.  The fine and replace kernels' work is
-counted the same way from their networks.
+networks, per output -- plus the data-dependent sparse work: at each S'
+item either the standalone med5 network (fine-structure items, and every
+item in the separable-median mode) or the lo test decided by rank (one
+comparison per window value, 25), and at each F evaluation either the med7
+network (float32 frames) or the objlim test decided by rank (49
+comparisons).  Halo recomputation is not counted.  The fine and replace
+kernels' work is counted the same way from their networks.
 """
 from __future__ import annotations
 
 import functools
 import importlib.util
 import os
+
+# Comparisons of a rank test: one per window value (5x5 for the lo test of S',
+# 7x7 for the objlim test of F).
+RANK_TEST_LO = 25
+RANK_TEST_OBJLIM = 49
 
 _GEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "gen_networks.py")
 
@@ -33,40 +41,30 @@ def counts() -> dict:
     return c
 
 
-def detect_minmax_ops(profile: dict) -> int:
-    """Min/max operations of all detect launches of one request: the dense
-    networks at the tile pixels the core kernel computed (a level skips the
-    tiles whose inputs did not change) and med5 at each S' evaluation."""
-    c = counts()
-    px = profile.get("px_core", profile["px_iterations"])
-    return int(px * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
-               + profile["n_sprime"] * c["med5x5"])
-
-
 def detect_work(profile: dict, packed: bool) -> dict:
-    """Algorithmic min/max work of the core launches of one request, split by
+    """Algorithmic ALU work of the core launches of one request, split by
     kind and counted in instructions as well as element operations.
 
     * dense: the shared-block med5 (noise model) and med3 networks at every
       tile pixel the core kernel computed; on uint16 frames one packed
       min/max.u16x2 instruction serves two outputs (``packed``);
-    * sprime: the standalone med5 of S at each S' evaluation (float keys);
-    * fine: the med7 of med3 at each fine-structure evaluation (one lane).
+    * sprime: the standalone med5 of S at each S' evaluation that runs the
+      network, and 25 comparisons at each one decided by rank (float keys);
+    * fine: the med7 of med3 at each fine-structure evaluation that runs the
+      network, and 49 comparisons at each one decided by rank (one lane).
     The masked-median replacement is not counted (its per-tile list includes
-    the halo that neighbouring tiles recompute)."""
+    the halo that neighbouring tiles recompute).  ``*_as_networks`` gives the
+    same medians costed as if every one ran its network."""
     c = counts()
     px = profile.get("px_core", profile["px_iterations"])
     dense = px * (c["dense_med5_per_px"] + c["dense_med3_per_px"])
-    sprime = profile["n_sprime"] * c["med5x5"]
-    fine = profile["n_fine"] * c["med7x7"]
-    return {"dense_elem": dense, "dense_instr": dense / 2 if packed else dense,
+    n_s, n_f = profile["n_sprime"], profile["n_fine"]
+    n_s_net = profile.get("n_sprime_net", n_s)
+    n_f_net = profile.get("n_fine_net", n_f)
+    sprime = n_s_net * c["med5x5"] + (n_s - n_s_net) * RANK_TEST_LO
+    fine = n_f_net * c["med7x7"] + (n_f - n_f_net) * RANK_TEST_OBJLIM
+    dense_i = dense / 2 if packed else dense
+    return {"dense_elem": dense, "dense_instr": dense_i,
             "sprime_instr": sprime, "fine_instr": fine,
-            "instr": (dense / 2 if packed else dense) + sprime + fine}
-
-
-def fine_minmax_ops(profile: dict) -> int:
-    return int(profile["n_fine"] * counts()["fine_per_px"])
-
-
-def replace_minmax_ops(profile: dict) -> int:
-    return int(profile["n_replace"] * counts()["med5x5"])
+            "instr": dense_i + sprime + fine,
+            "instr_as_networks": dense_i + n_s * c["med5x5"] + n_f * c["med7x7"]}
