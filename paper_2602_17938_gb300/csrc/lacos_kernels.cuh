@@ -97,6 +97,7 @@ struct Geo {
   using XR6 = Reg<6, 8>;  // core: X0 and M_{k-1}
   using XR3 = Reg<3, 8>;  // finalize
   static_assert(TW % 32 == 0 && TH % 8 == 0 && NT % 32 == 0, "tile geometry");
+  static_assert((TH & (TH - 1)) == 0 && (TW & (TW - 1)) == 0, "tile sides are powers of two (mark_tiles shifts)");
 };
 // The core variants' tile shapes.
 using G32x64 = Geo<32, 64, 256>;
@@ -1515,7 +1516,7 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
                                                            unsigned* head) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_item;
-  __shared__ int s_run;
+  __shared__ int s_run, s_fi;
   constexpr int kDtype = std::is_same<XT, uint16_t>::value ? 1 : 0;
   __shared__ TileCounts acc;       // sums of the tiles of frame acc_st so far (thread 0)
   __shared__ FrameState* acc_st;
@@ -1526,9 +1527,10 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned item = item_begin + atomicAdd(head, 1u);
-      int run = 0;
+      int run = 0, fi = 0;
       if (item < item_end) {
-        const FrameDesc& f = fr[frame_of(fr, nframes, item)];
+        fi = frame_of(fr, nframes, item);
+        const FrameDesc& f = fr[fi];
         run = f.dtype == kDtype && iteration_runs(f, k);
         if (run && k > 1) {  // levels after the first: only the tiles whose inputs changed
           const unsigned t = item - f.tile_begin;
@@ -1539,6 +1541,7 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
       }
       s_item = item;
       s_run = run;
+      s_fi = fi;
     }
     __syncthreads();
     const unsigned item = s_item;
@@ -1546,7 +1549,7 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
     __syncthreads();
     if (item >= item_end) break;
     if (!run) continue;
-    const FrameDesc& f = fr[frame_of(fr, nframes, item)];
+    const FrameDesc& f = fr[s_fi];
     const TileCounts c = core_tile<G, XT>(f, k, (int)(item - f.tile_begin),
                                          *reinterpret_cast<CoreSmemT<G, XT>*>(smem_raw));
     if (threadIdx.x == 0) {
@@ -1578,16 +1581,17 @@ __global__ void __launch_bounds__(G::NT, MINB) core_kernel(const FrameDesc* __re
 // reads and clears the mark; a tile that needs a wide window is marked for
 // good.
 
-__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Marks for level kn every tile whose rows/columns +-6 hold a set bit of
-// `bits`, the new flags of word w of row y.
-__device__ __forceinline__ void mark_tiles(const FrameDesc& f, int kn, int y, int w, uint32_t bits) {
+// `bits`, the new flags of word w of row y: tile rows floor((y-6)/th) ..
+// floor((y+6)/th), likewise for the columns of the set bits.  The core tile
+// sides are powers of two (sh_h, sh_w: their log2), so an arithmetic shift
+// is that floor, also for negative numerators.
+__device__ __forceinline__ void mark_tiles(const FrameDesc& f, int kn, int y, int w, uint32_t bits, int sh_h,
+                                           int sh_w, int tiles_y) {
   const int x_lo = w * 32 + __ffs(bits) - 1, x_hi = w * 32 + 31 - __clz(bits);
-  const int th = f.th, tw = f.tw;  // the core tiles of the request
-  const int tiles_y = (f.ny + th - 1) / th;
-  const int ty0 = max(0, floordiv(y - th - 6, th) + 1), ty1 = min(tiles_y - 1, (y + 6) / th);
-  const int tx0 = max(0, floordiv(x_lo - tw - 6, tw) + 1), tx1 = min(f.tiles_x - 1, (x_hi + 6) / tw);
+  const int ty0 = max(0, (y - 6) >> sh_h), ty1 = min(tiles_y - 1, (y + 6) >> sh_h);
+  const int tx0 = max(0, (x_lo - 6) >> sh_w), tx1 = min(f.tiles_x - 1, (x_hi + 6) >> sh_w);
   uint8_t* d = f.tflags + (size_t)(kn & 1) * tiles_of(f);
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) d[ty * f.tiles_x + tx] = 1;
@@ -1688,6 +1692,8 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
   __syncthreads();
   bool any = false;
   uint32_t* Mn = (k & 1) ? f.mbuf1 : f.mbuf0;
+  const int sh_h = __ffs(f.th) - 1, sh_w = __ffs(f.tw) - 1;  // the request's core tiles
+  const int tiles_y = (ny + f.th - 1) >> sh_h;
 #pragma unroll
   for (int p = 0; p < GB_WPT; ++p) {
     const int i = p * NT + tid, ty = i / GB_W, tx = i % GB_W;
@@ -1700,7 +1706,7 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
       Mn[(size_t)y * wpr + w] = mp[p] | g2;
       const uint32_t fresh = g2 & ~mp[p];
       any = any || fresh != 0;
-      if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh);
+      if (fresh && k < f.niter) mark_tiles(f, k + 1, y, w, fresh, sh_h, sh_w, tiles_y);
     }
   }
   // Only "did level k flag anything" is used (early stop): one flag store
