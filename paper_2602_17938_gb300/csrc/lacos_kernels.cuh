@@ -293,32 +293,40 @@ template <> struct KeyOf<uint16_t> {
 };
 
 // Masked 5x5 median at shared-memory index c of X (pitch P) with flags Mb:
-// the lower median of the unflagged members.  Flagged members are replaced
-// by sentinels, the first (12 - (n-1)/2) by the low sentinel and the rest by
-// the high one, so that the rank-12 element of the 25 is the rank-(n-1)/2
-// unflagged value.  Returns false when no member is unflagged.
+// the lower median of the unflagged members.  With k members flagged and
+// n = 25 - k unflagged, the rank-12 element of the 25 is the rank-(n-1)/2
+// unflagged value when ceil(k/2) flagged members are taken as a low sentinel
+// and the other floor(k/2) as a high one.  Which flagged members get which
+// does not matter (the rank is a function of the multiset), so the i-th
+// flagged member in row-major order takes the low sentinel for even i and
+// the high one for odd i: bit j of `odd`, the parity of the flagged members
+// before j, is an exclusive prefix XOR of the flag bits, with no running
+// count.  Returns false when no member is unflagged.
 template <class XT>
 __device__ __forceinline__ bool maskmed5(const XT* X, const uint8_t* Mb, int P, int c, XT& out) {
   using KT = KeyOf<XT>;
   using K = typename KT::K;
-  int n = 0;
+  uint32_t b = 0;  // bit j: window member j (row-major) is flagged
 #pragma unroll
   for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
-    for (int dx = -2; dx <= 2; ++dx) n += Mb[c + dy * P + dx] ? 0 : 1;
-  if (n == 0) return false;
-  const int plo = 12 - (n - 1) / 2;
+    for (int dx = -2; dx <= 2; ++dx) b |= (uint32_t)(Mb[c + dy * P + dx] != 0) << ((dy + 2) * 5 + dx + 2);
+  if (b == 0x1ffffffu) return false;
+  uint32_t x = b;  // inclusive prefix XOR
+  x ^= x << 1;
+  x ^= x << 2;
+  x ^= x << 4;
+  x ^= x << 8;
+  x ^= x << 16;
+  const uint32_t odd = x << 1;  // exclusive
   K v[25];
-  int seen = 0;
 #pragma unroll
   for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
     for (int dx = -2; dx <= 2; ++dx) {
-      const int q = c + dy * P + dx;
-      const bool fl = Mb[q] != 0;
-      const K s = (seen < plo) ? KT::lo() : KT::hi();
-      seen += fl ? 1 : 0;
-      v[(dy + 2) * 5 + dx + 2] = fl ? s : KT::key(X[q]);
+      const int j = (dy + 2) * 5 + dx + 2;
+      const K s = ((odd >> j) & 1u) ? KT::hi() : KT::lo();
+      v[j] = ((b >> j) & 1u) ? s : KT::key(X[c + dy * P + dx]);
     }
   K o;
   med5x5<K>(v, &o);
