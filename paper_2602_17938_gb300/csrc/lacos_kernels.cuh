@@ -1786,7 +1786,10 @@ __device__ unsigned finalize_tile(const FrameDesc& f, int tix, FinalSmemT<FG, XT
     sm.X[c] = v;
   }
   __syncthreads();
-  const bool vec = (f.nx & 3) == 0;
+  // 16-byte stores of the cleaned frame and 4-byte stores of the mask where
+  // the row pitch and the caller's output pointers allow them.
+  const bool vec = (f.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(f.clean_out) & 15u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(f.mask_out) & 3u) == 0;
   for (int qd = tid; qd < TH * TW / 4; qd += NT) {
     const int ly = qd / (TW / 4), lx = (qd % (TW / 4)) * 4;
     const int gy = oy + ly, gx = ox + lx;

@@ -381,3 +381,21 @@ def test_core_variants_on_the_batched_path(ctx):
                 assert (per[i].iters_run, per[i].n_flagged) == (it_ref, nf_ref), (v, i)
     finally:
         ctx.set_core_variant(v0)
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.float32])
+def test_unaligned_output_buffers(ctx, dtype):
+    # The ABI takes any output pointers: a cleaned frame that is not 16-byte aligned and a mask
+    # that is not 4-byte aligned (views one element into larger buffers) take the finalize
+    # kernel's scalar stores and must give the same result as aligned buffers.
+    from paper_2602_17938_gb300 import lacos
+    ny, nx = 130, 256  # nx a multiple of 4: aligned outputs would take the vector stores
+    f = noisy_with_hits(ny, nx, seed=77, dtype=dtype)
+    cbuf = torch.empty(ny * nx + 1, dtype=torch.float32, device="cuda")
+    mbuf = torch.empty(ny * nx + 1, dtype=torch.uint8, device="cuda")
+    clean, mask = cbuf[1:].view(ny, nx), mbuf[1:].view(ny, nx)
+    assert clean.data_ptr() % 16 != 0 and mask.data_ptr() % 4 != 0
+    p = lacos.make_params(1.0, 1.5)
+    res = ctx.wait(ctx.submit(lacos.to_device(f), p, mask, clean))
+    torch.cuda.synchronize()
+    assert_same(f, 1.0, 1.5, (mask.cpu().numpy(), clean.cpu().numpy(), res))
