@@ -375,14 +375,20 @@ def run_small_frame(args, dev, with_oracle):
     p = lacos.make_params(spec.gain, spec.readnoise, spec.satlevel, spec.sigclip, spec.sigfrac, spec.objlim,
                           spec.niter)
     stream = torch.cuda.current_stream(dev)
+    from paper_2602_17938_gb300 import autotune
     with lacos.Context(dev.index or 0) as ctx:
+        # The core variant of this size class (tile shape and occupancy), as the library's
+        # users would pick it: a frame of 0.26 Mpx fills few SMs with the large tiles.
+        variant, variant_ms = autotune.tune(ctx, d, p, m, c, reps=5)
+
         def one():
             ctx.wait(ctx.submit(d, p, m, c, stream))
         ms = _time_passes(one, 50, stream)
         r = ctx.wait(ctx.submit(d, p, m, c, stream))
     out = {"workload": "512x512 f32 (seed 0: 20 stars, 200 tracks, 0.1% hot pixels), niter=4, one frame per call",
            "ms_per_request": ms, "mpix_per_s": spec.npix / 1e6 / (ms / 1e3), "n_flagged": r.n_flagged,
-           "iters_run": r.iters_run, "l2": "not flushed (the frame and outputs are 6 MB)"}
+           "iters_run": r.iters_run, "l2": "not flushed (the frame and outputs are 6 MB)",
+           "core_variant": {"chosen": variant, "ms_per_variant": variant_ms}}
     if with_oracle:
         import oracle
         oracle.build()
