@@ -33,7 +33,7 @@ WORKLOAD = "lacosmic_9576x6388_u16_niter4"
 # DRAM bytes (read + write) per core_kernel launch from one ncu capture on
 # this workload, keyed by kernel_source_sha() of the captured build; any other
 # source reports null (the counters no longer describe the kernel).
-NCU_CORE_TRAFFIC = {"4c9b49899ee65d6d": 131_792_640 + 17_348_864}
+NCU_CORE_TRAFFIC = {"b9364813600865ce": 131_750_912 + 17_399_552}
 
 
 def kernel_source_sha() -> str:

@@ -1642,14 +1642,19 @@ __device__ __forceinline__ int frame_of_gblk(const FrameDesc* fr, int nframes, u
 // 1-word halo) are staged in shared memory; each thread then forms
 // g2 = dil3(g1) & lo for its words, M_k = M_{k-1} | g2, and counts new flags.
 // Every global load of the block (candidate, sig, lo and mask words) is
-// issued up front, so the block waits for one memory round trip.
+// issued up front, so the block waits for one memory round trip.  Bounded
+// for six resident blocks per SM (40 registers, no spills).
 template <class GG>
-__global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
+__global__ void __launch_bounds__(kBlock, 6) grow_kernel(const FrameDesc* __restrict__ fr, int nframes,
                                                       unsigned total_blocks, int k) {
   constexpr int NT = kBlock, GB_H = GG::H, GB_W = GG::W, GB_WPT = GG::WPT;
-  constexpr int CW = GB_W + 4, CN = (GB_H + 4) * CW;  // candidate region
-  constexpr int GW = GB_W + 2, GN = (GB_H + 2) * GW;  // g1 region
-  constexpr int CP = (CN + NT - 1) / NT, GP = (GN + NT - 1) / NT;
+  constexpr int CW = GB_W + 4;  // candidate region: GB_H + 4 rows of CW words
+  constexpr int GW = GB_W + 2;  // g1 region: GB_H + 2 rows of GW words
+  // The halo regions in two dimensions: a thread keeps one column of a region
+  // and steps its rows, so each load costs a row test and an address, not a
+  // division by the region's width.
+  constexpr int CR = NT / CW, CPASS = (GB_H + 4 + CR - 1) / CR;  // candidate rows per pass, passes
+  constexpr int GR = NT / GW, GPASS = (GB_H + 2 + GR - 1) / GR;  // g1 rows per pass, passes
   __shared__ uint32_t C[GB_H + 4][CW];
   __shared__ uint32_t G1[GB_H + 2][GW];
   const int tid = threadIdx.x;
@@ -1661,16 +1666,19 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
   const int y0 = (int)(b / (unsigned)f.gblk_x) * GB_H, w0 = (int)(b % (unsigned)f.gblk_x) * GB_W;
   const int ny = f.ny, wpr = f.wpr;
   const uint32_t* Mp = ((k - 1) & 1) ? f.mbuf1 : f.mbuf0;
-  uint32_t cw[CP], sw[GP];
+  const int cc = tid % CW, cr0 = tid / CW, gc = tid % GW, gr0 = tid / GW;
+  const int cwc = w0 - 2 + cc, gwc = w0 - 1 + gc;  // frame word columns of this thread
+  const bool ccol = cr0 < CR && cwc >= 0 && cwc < wpr, gcol = gr0 < GR && gwc >= 0 && gwc < wpr;
+  uint32_t cw[CPASS], sw[GPASS];
 #pragma unroll
-  for (int p = 0; p < CP; ++p) {
-    const int i = p * NT + tid;
-    cw[p] = i < CN ? plane_word(f.p_cand, ny, wpr, y0 - 2 + i / CW, w0 - 2 + i % CW) : 0u;
+  for (int p = 0; p < CPASS; ++p) {
+    const int r = cr0 + p * CR, y = y0 - 2 + r;
+    cw[p] = (ccol && r < GB_H + 4 && y >= 0 && y < ny) ? __ldg(f.p_cand + (size_t)y * wpr + cwc) : 0u;
   }
 #pragma unroll
-  for (int p = 0; p < GP; ++p) {
-    const int i = p * NT + tid;
-    sw[p] = i < GN ? plane_word(f.p_sig, ny, wpr, y0 - 1 + i / GW, w0 - 1 + i % GW) : 0u;
+  for (int p = 0; p < GPASS; ++p) {
+    const int r = gr0 + p * GR, y = y0 - 1 + r;
+    sw[p] = (gcol && r < GB_H + 2 && y >= 0 && y < ny) ? __ldg(f.p_sig + (size_t)y * wpr + gwc) : 0u;
   }
   uint32_t lo[GB_WPT], mp[GB_WPT];
 #pragma unroll
@@ -1680,21 +1688,24 @@ __global__ void __launch_bounds__(kBlock) grow_kernel(const FrameDesc* __restric
     lo[p] = own ? __ldg(f.p_lo + (size_t)y * wpr + w) : 0u;
     mp[p] = own ? __ldg(Mp + (size_t)y * wpr + w) : 0u;
   }
+  if (cr0 < CR) {
 #pragma unroll
-  for (int p = 0; p < CP; ++p) {
-    const int i = p * NT + tid;
-    if (i < CN) C[i / CW][i % CW] = cw[p];
+    for (int p = 0; p < CPASS; ++p) {
+      const int r = cr0 + p * CR;
+      if (r < GB_H + 4) C[r][cc] = cw[p];
+    }
   }
   __syncthreads();
+  if (gr0 < GR) {
 #pragma unroll
-  for (int p = 0; p < GP; ++p) {
-    const int i = p * NT + tid;
-    if (i < GN) {
-      const int r = i / GW, c = i % GW;
-      uint32_t d = 0;
+    for (int p = 0; p < GPASS; ++p) {
+      const int r = gr0 + p * GR;
+      if (r < GB_H + 2) {
+        uint32_t d = 0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][c], C[r + a][c + 1], C[r + a][c + 2]);
-      G1[r][c] = d & sw[p];
+        for (int a = 0; a < 3; ++a) d |= hdil(C[r + a][gc], C[r + a][gc + 1], C[r + a][gc + 2]);
+        G1[r][gc] = d & sw[p];
+      }
     }
   }
   __syncthreads();
