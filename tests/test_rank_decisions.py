@@ -147,3 +147,49 @@ def test_a_slip_in_the_rank_is_caught():
         Sc = f32(np.sort(w)[11] + lo + f32(0.01)) if rng.integers(0, 2) else Sc
         wrong += (int(sum(f32(Sc - v) > lo for v in w)) >= 12) != lo_by_median(Sc, w, lo)
     assert wrong > 0
+
+
+def _windows(A, r):
+    """The (2r+1)^2 clamped-window values of every pixel of A, shape (K*K, ny, nx)."""
+    P = np.pad(A, r, mode="edge")
+    ny, nx = A.shape
+    return np.stack([P[dy:dy + ny, dx:dx + nx] for dy in range(2 * r + 1) for dx in range(2 * r + 1)])
+
+
+def test_rank_decisions_on_a_synthetic_frame():
+    # Realistic value fields: a uint16 frame of the 61-Mpx recipe (stars, tracks, salt and pepper)
+    # at its first level, S = L+ / (2N) with N from the exact 5x5 median, S' items where S
+    # exceeds the lower threshold, med3 and the 7x7 median of med3 from the oracle.  At every
+    # item the lo test by rank must equal the test at the oracle's med5(S), and at every fine
+    # item with S' > sigclip the objlim test by rank must equal the test at its med7.
+    import oracle
+    from paper_2602_17938_gb300 import synth
+    spec = synth.FrameSpec(**{**synth.config_specs(1)[0].__dict__, "ny": 192, "nx": 256, "seed": (1, 900),
+                              "n_stars": 12, "n_tracks": 500})
+    X = synth.make_frame(spec).astype(np.float32)
+    g, rn2 = f32(spec.gain), f32(spec.readnoise) * f32(spec.readnoise)
+    m5 = oracle.median(X, 5)
+    N = (np.sqrt(np.maximum(g * m5, f32(1e-4)) + rn2) / g).astype(f32)
+    S = (oracle.lplus(X) / (N + N)).astype(f32)
+    lo, sigclip, objlim = f32(spec.sigfrac * spec.sigclip), f32(spec.sigclip), f32(spec.objlim)
+    mS = oracle.median(S, 5)
+    items = np.argwhere(S > min(lo, sigclip))
+    assert len(items) > 2000
+    W5 = _windows(S, 2)
+    for y, x in items:
+        assert lo_by_rank(S[y, x], W5[:, y, x], lo) == bool(f32(S[y, x] - mS[y, x]) > lo), (y, x)
+    m3 = oracle.median(X, 3)
+    m7 = oracle.median(m3, 7)
+    W7 = _windows(m3, 3).astype(np.int64)
+    fine = 0
+    for y, x in items:
+        sp = f32(S[y, x] - mS[y, x])
+        if not (S[y, x] > sigclip and sp > sigclip):
+            continue
+        fine += 1
+        got, steps = objlim_by_rank(sp, N[y, x], int(m3[y, x]), W7[:, y, x], objlim, True)
+        assert got is not None and steps <= 3
+        diff = f32(m3[y, x] - m7[y, x])
+        F = max(f32(diff / N[y, x]), f32(0.01))
+        assert got == bool(f32(sp / F) > objlim), (y, x)
+    assert fine > 200
